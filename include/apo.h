@@ -1,0 +1,174 @@
+/*
+ * apo.h -- C ABI of libapo.so, a GB300 (sm_103a) implementation of the
+ * Artificial Protozoa Optimizer (APO) population update described in
+ * "cuAPO: A CUDA-based Parallelization of Artificial Protozoa Optimizer"
+ * (Soliya and Jain): Sec. 3 (Eq. 1-13), Algorithm 1, and the thresholding
+ * application of Sec. 5.2.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named d_* are CUDA device pointers on the current device;
+ *     every other pointer is host memory.  The caller owns every buffer it
+ *     passes; the library owns apo_problem objects and its internal
+ *     workspace.
+ *   - Positions are float32, row-major [n][D] (row stride D, no padding).
+ *   - Fitness values are float32, except for APO_OBJ_OTSU, whose fitness
+ *     (the negated between-class variance) is float64.  Arguments typed
+ *     `void* d_F` follow this rule.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     documented as stream-ordered only enqueue work; calls documented as
+ *     synchronous return after their host outputs are written.
+ *   - Errors are reported by the return code only; nothing is thrown and
+ *     nothing exits.  apo_last_error() returns a static, thread-local detail
+ *     string for the last failing call of the calling thread.
+ *   - Minimisation: a smaller fitness is better.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed, run),
+ * counter = (iteration, protozoon rank, dimension pair, slot).  Identical
+ * (seed, run, params, problem) give identical results on a given build.
+ */
+#ifndef APO_H
+#define APO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum apo_status {
+    APO_OK = 0,
+    APO_ERR_INVALID_ARG = 1, /* an argument is out of its documented range     */
+    APO_ERR_CUDA = 2,        /* a CUDA runtime call or a kernel launch failed   */
+    APO_ERR_OOM = 3,         /* device or host allocation failed               */
+    APO_ERR_TIMEOUT = 4,     /* a device-side wait exceeded its limit           */
+    APO_ERR_UNSUPPORTED = 5, /* valid, but outside what this build supports     */
+    APO_ERR_INTERNAL = 6
+} apo_status;
+
+/* Objective families.  z = M (x - o) with M a D x D rotation (row-major) and
+ * o a shift; both are optional (identity / zero when NULL). */
+typedef enum apo_objective_kind {
+    APO_OBJ_SPHERE = 0,      /* sum z_i^2 (Eq. 14)                                     */
+    APO_OBJ_ELLIPTIC = 1,    /* sum 10^(6 (i-1)/(D-1)) z_i^2                          */
+    APO_OBJ_ROSENBROCK = 2,  /* sum_{i<D} 100 (z_{i+1} - z_i^2)^2 + (z_i - 1)^2        */
+    APO_OBJ_RASTRIGIN = 3,   /* sum z_i^2 - 10 cos(2 pi z_i) + 10                      */
+    APO_OBJ_HYBRID = 4,      /* w = z[perm]; ceil(.3D) elliptic, ceil(.3D) Rosenbrock,
+                                rest Rastrigin                                        */
+    APO_OBJ_COMPOSITION = 5, /* n_comp components, component k = form 1 + (k mod 4)
+                                with its own o_k, M_k, perm_k; weights
+                                w_k = exp(-||x-o_k||^2 / (2 D sigma_k^2));
+                                f = sum w_k (g_k + bias_k) / sum w_k                 */
+    APO_OBJ_OTSU = 6         /* -sigma_B^2 of an image histogram, thresholds
+                                t_j = clamp(floor(x_j), 0, 255) sorted (Sec. 5.2)     */
+} apo_objective_kind;
+
+#define APO_MAX_COMPONENTS 10
+#define APO_MAX_DIM 256
+#define APO_MAX_OTSU_THRESHOLDS 31
+
+typedef struct apo_objective_desc {
+    int kind;                  /* apo_objective_kind                              */
+    const float* shift;        /* [D] (composition: [n_comp*D]); NULL = 0          */
+    const float* rotation;     /* [D*D] row-major (composition: [n_comp*D*D]);
+                                  NULL = identity (not allowed for composition)    */
+    const int32_t* perm;       /* hybrid: [D] permutation of 0..D-1; composition:
+                                  [n_comp*D] (used by its hybrid components)      */
+    int n_comp;                /* composition: 1..APO_MAX_COMPONENTS               */
+    const double* comp_sigma;  /* composition: [n_comp], > 0                      */
+    const double* comp_bias;   /* composition: [n_comp]                           */
+    const int32_t* hist;       /* Otsu: [256] pixel counts (host, or device when
+                                  hist_on_device != 0); total count > 0            */
+    int hist_on_device;
+} apo_objective_desc;
+
+/* Algorithm 1 inputs.  Validation: ps >= 2, 1 <= np, 2*np < ps,
+ * 0 <= pf_max <= 1, max_iter >= 1, pdr_form in {0, 1}. */
+typedef struct apo_params {
+    int ps;           /* population size                                       */
+    int np;           /* neighbour pairs in Eq. 6 and Eq. 8                     */
+    double pf_max;    /* maximum proportion fraction (Eq. 11)                   */
+    int max_iter;     /* iterations (MaxFEs of Algorithm 1 counts iterations)   */
+    uint32_t seed;    /* Philox key word 0                                      */
+    uint32_t run;     /* Philox key word 1 (independent stream per run)         */
+    int pdr_form;     /* 0: Eq. 13 as printed, p_dr = (1 - cos((1-i/ps) pi))/2;
+                         1: the mirrored (1 + cos((1-i/ps) pi))/2               */
+} apo_params;
+
+typedef struct apo_problem apo_problem;
+
+/* Creates a problem: D dimensions (1..APO_MAX_DIM; Otsu: 1..31 thresholds),
+ * bounds lb < ub per dimension (the Xmin, Xmax of Eq. 1-2), and the
+ * objective.  Every array is copied to the device; the caller may free its
+ * buffers on return.  Synchronous.  *out is NULL on failure. */
+apo_status apo_problem_create(int D, const double* lb, const double* ub,
+                              const apo_objective_desc* obj, apo_problem** out);
+
+/* Releases a problem (NULL is a no-op).  Waits for the device to finish work
+ * that may still read it. */
+void apo_problem_destroy(apo_problem* prob);
+
+int apo_problem_dim(const apo_problem* prob);
+
+/* A whole run of Algorithm 1: initialisation, params->max_iter iterations of
+ * sort, Dr selection (Eq. 11), dormancy / reproduction / autotrophic /
+ * heterotrophic candidates (Eq. 1-10, 12-13), bound clamp, evaluation,
+ * greedy replacement.  Outputs (host): best_x [D], *best_f, and curve
+ * [max_iter + 1] (curve[t] = best fitness after iteration t, curve[0] after
+ * initialisation; NULL = not wanted).  Synchronous. */
+apo_status apo_run(const apo_problem* prob, const apo_params* params, void* stream,
+                   float* best_x, double* best_f, float* curve);
+
+/* Same as apo_run with device outputs: d_best_x [D], d_best_f [1],
+ * d_curve [max_iter + 1] or NULL.  Stream-ordered. */
+apo_status apo_run_device(const apo_problem* prob, const apo_params* params, void* stream,
+                          float* d_best_x, double* d_best_f, float* d_curve);
+
+/* n_runs independent runs in as few launches as possible (a persistent
+ * work-queue launch for runs whose population fits in shared memory, a
+ * cooperative grid launch for the rest).  Run k uses probs[k] and params[k]
+ * and writes d_best_x[k*x_stride .. +D), d_best_f[k], and, when d_curves is
+ * not NULL, d_curves[k*curve_stride .. + max_iter + 1).  x_stride >= max D,
+ * curve_stride >= max (max_iter + 1).  Stream-ordered. */
+apo_status apo_run_batch(const apo_problem* const* probs, const apo_params* params, int n_runs,
+                         void* stream, float* d_best_x, int x_stride, double* d_best_f,
+                         float* d_curves, int curve_stride);
+
+/* Test hook: iteration `iter` (1..max_iter) of Algorithm 1 applied to a given
+ * state.  d_X [ps*D] and d_F [ps] hold the population in its current order;
+ * on return they hold it in the rank order of this iteration's fitness sort
+ * (ascending, ties kept in current order) after the greedy replacement.
+ * Stream-ordered. */
+apo_status apo_step(const apo_problem* prob, const apo_params* params, int iter,
+                    void* stream, float* d_X, void* d_F);
+
+/* Evaluates the objective at n points d_X [n*D] into d_F [n].  Stream-ordered. */
+apo_status apo_evaluate(const apo_problem* prob, void* stream, const float* d_X, int n,
+                        void* d_F);
+
+/* Sec. 4.1 step 6 on n protozoa: clamp d_Xnew [n*D] to the bounds (in place),
+ * evaluate it into d_Fnew [n], and replace d_X / d_F rows where
+ * f(Xnew) < f(X).  Stream-ordered. */
+apo_status apo_clamp_eval_select(const apo_problem* prob, void* stream, int n, float* d_X,
+                                 void* d_F, float* d_Xnew, void* d_Fnew);
+
+/* 256-bin histograms of n_images 8-bit images stored back to back
+ * (d_pixels [n_images * n_pixels_per_image]) into d_hist [n_images*256]
+ * (int32 counts, overwritten; bit-exact).  n_pixels_per_image < 2^31.
+ * Stream-ordered. */
+apo_status apo_histogram_u8(const uint8_t* d_pixels, int64_t n_pixels_per_image, int n_images,
+                            int32_t* d_hist, void* stream);
+
+/* Test hook: the device Philox4x32-10 on n counters d_ctr [n*4] with key
+ * (key0, key1) into d_out [n*4].  Stream-ordered. */
+apo_status apo_philox4x32_10(const uint32_t* d_ctr, uint32_t key0, uint32_t key1, int n,
+                             uint32_t* d_out, void* stream);
+
+const char* apo_status_string(apo_status status);
+const char* apo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APO_H */

@@ -1,0 +1,226 @@
+"""Thin ctypes binding of libapo.so (declared in include/apo.h).
+
+Every function keeps the C name and only marshals arguments: torch tensors
+are passed as raw device pointers, streams as ``cudaStream_t`` handles.  All
+of the optimiser's work runs in the library's CUDA kernels.  Importing this
+module loads libapo.so and raises ImportError when it is missing; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libapo.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libapo.so is not built (run paper_2510_14982_gb300/build.py or "
+                      "__graft_entry__.build()); the APO path has no CPU fallback")
+_lib = C.CDLL(LIB_PATH)
+
+APO_OK, APO_ERR_INVALID_ARG, APO_ERR_CUDA, APO_ERR_OOM, APO_ERR_TIMEOUT, APO_ERR_UNSUPPORTED, APO_ERR_INTERNAL = range(7)
+(APO_OBJ_SPHERE, APO_OBJ_ELLIPTIC, APO_OBJ_ROSENBROCK, APO_OBJ_RASTRIGIN, APO_OBJ_HYBRID,
+ APO_OBJ_COMPOSITION, APO_OBJ_OTSU) = range(7)
+
+# every entry point declared in include/apo.h
+EXPORTS = ("apo_problem_create", "apo_problem_destroy", "apo_problem_dim", "apo_run", "apo_run_device",
+           "apo_run_batch", "apo_step", "apo_evaluate", "apo_clamp_eval_select", "apo_histogram_u8",
+           "apo_philox4x32_10", "apo_status_string", "apo_last_error")
+
+
+class apo_objective_desc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("shift", C.POINTER(C.c_float)), ("rotation", C.POINTER(C.c_float)),
+                ("perm", C.POINTER(C.c_int32)), ("n_comp", C.c_int),
+                ("comp_sigma", C.POINTER(C.c_double)), ("comp_bias", C.POINTER(C.c_double)),
+                ("hist", C.POINTER(C.c_int32)), ("hist_on_device", C.c_int)]
+
+
+class apo_params(C.Structure):
+    _fields_ = [("ps", C.c_int), ("np", C.c_int), ("pf_max", C.c_double), ("max_iter", C.c_int),
+                ("seed", C.c_uint32), ("run", C.c_uint32), ("pdr_form", C.c_int)]
+
+
+_P = C.c_void_p
+_lib.apo_problem_create.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(apo_objective_desc), C.POINTER(_P)]
+_lib.apo_problem_create.restype = C.c_int
+_lib.apo_problem_destroy.argtypes = [_P]
+_lib.apo_problem_destroy.restype = None
+_lib.apo_problem_dim.argtypes = [_P]
+_lib.apo_problem_dim.restype = C.c_int
+_lib.apo_run.argtypes = [_P, C.POINTER(apo_params), _P, C.POINTER(C.c_float), C.POINTER(C.c_double),
+                         C.POINTER(C.c_float)]
+_lib.apo_run_device.argtypes = [_P, C.POINTER(apo_params), _P, _P, _P, _P]
+_lib.apo_run_batch.argtypes = [C.POINTER(_P), C.POINTER(apo_params), C.c_int, _P, _P, C.c_int, _P, _P, C.c_int]
+_lib.apo_step.argtypes = [_P, C.POINTER(apo_params), C.c_int, _P, _P, _P]
+_lib.apo_evaluate.argtypes = [_P, _P, _P, C.c_int, _P]
+_lib.apo_clamp_eval_select.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
+_lib.apo_histogram_u8.argtypes = [_P, C.c_int64, C.c_int, _P, _P]
+_lib.apo_philox4x32_10.argtypes = [_P, C.c_uint32, C.c_uint32, C.c_int, _P, _P]
+for _f in ("apo_run", "apo_run_device", "apo_run_batch", "apo_step", "apo_evaluate", "apo_clamp_eval_select",
+           "apo_histogram_u8", "apo_philox4x32_10"):
+    getattr(_lib, _f).restype = C.c_int
+_lib.apo_status_string.argtypes = [C.c_int]
+_lib.apo_status_string.restype = C.c_char_p
+_lib.apo_last_error.argtypes = []
+_lib.apo_last_error.restype = C.c_char_p
+
+
+class ApoError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = "%s: %s (%s)" % (where, _lib.apo_status_string(status).decode(), _lib.apo_last_error().decode())
+        super().__init__(msg)
+
+
+def _check(rc: int, where: str):
+    if rc != APO_OK:
+        raise ApoError(rc, where)
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (None -> NULL)."""
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _np_ptr(a, ctype):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ctype))
+
+
+def apo_status_string(status: int) -> str:
+    return _lib.apo_status_string(status).decode()
+
+
+def apo_last_error() -> str:
+    return _lib.apo_last_error().decode()
+
+
+def apo_params_make(ps, np_=1, pf_max=0.1, max_iter=1000, seed=0, run=0, pdr_form=0) -> apo_params:
+    return apo_params(int(ps), int(np_), float(pf_max), int(max_iter), int(seed) & 0xFFFFFFFF,
+                      int(run) & 0xFFFFFFFF, int(pdr_form))
+
+
+class Problem:
+    """Owns an apo_problem handle (apo_problem_create / apo_problem_destroy)."""
+
+    def __init__(self, handle, D, kind):
+        self.handle, self.D, self.kind = handle, D, kind
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.apo_problem_destroy(h)
+            self.handle = None
+
+    @property
+    def fit_dtype(self):
+        import torch
+        return torch.float64 if self.kind == APO_OBJ_OTSU else torch.float32
+
+
+def apo_problem_create(D, lb, ub, kind, shift=None, rotation=None, perm=None, comp_sigma=None,
+                       comp_bias=None, hist=None, hist_device=None) -> Problem:
+    """apo_problem_create; array arguments are numpy arrays (hist_device: a torch int32 tensor)."""
+    lb = np.ascontiguousarray(np.broadcast_to(np.asarray(lb, np.float64), (D,)))
+    ub = np.ascontiguousarray(np.broadcast_to(np.asarray(ub, np.float64), (D,)))
+    keep = []
+
+    def f32(a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        keep.append(a)
+        return _np_ptr(a, C.c_float)
+
+    def arr(a, dt, ct):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return _np_ptr(a, ct)
+
+    n_comp = 0 if comp_sigma is None else len(comp_sigma)
+    desc = apo_objective_desc(int(kind), f32(shift), f32(rotation), arr(perm, np.int32, C.c_int32), n_comp,
+                              arr(comp_sigma, np.float64, C.c_double), arr(comp_bias, np.float64, C.c_double),
+                              None, 0)
+    if hist_device is not None:
+        desc.hist = C.cast(C.c_void_p(hist_device.data_ptr()), C.POINTER(C.c_int32))
+        desc.hist_on_device = 1
+    elif hist is not None:
+        desc.hist = arr(hist, np.int32, C.c_int32)
+    h = _P()
+    _check(_lib.apo_problem_create(int(D), _np_ptr(lb, C.c_double), _np_ptr(ub, C.c_double), C.byref(desc),
+                                   C.byref(h)), "apo_problem_create")
+    return Problem(h, int(D), int(kind))
+
+
+def problem_from_spec(spec) -> Problem:
+    """apo_problem_create from a ProblemSpec of the seeded input generators."""
+    return apo_problem_create(spec.D, spec.lb, spec.ub, spec.kind, spec.shift, spec.rot, spec.perm,
+                              spec.comp_sigma, spec.comp_bias,
+                              None if spec.hist is None else np.asarray(spec.hist, np.int32))
+
+
+def apo_run(prob: Problem, params: apo_params, stream=None, want_curve=True):
+    """apo_run (host outputs, synchronous): returns (best_x, best_f, curve)."""
+    best_x = np.empty(prob.D, np.float32)
+    best_f = C.c_double()
+    curve = np.empty(params.max_iter + 1, np.float32) if want_curve else None
+    _check(_lib.apo_run(prob.handle, C.byref(params), _stream(stream), _np_ptr(best_x, C.c_float),
+                        C.byref(best_f), _np_ptr(curve, C.c_float)), "apo_run")
+    return best_x, best_f.value, curve
+
+
+def apo_run_device(prob: Problem, params: apo_params, d_best_x, d_best_f, d_curve=None, stream=None):
+    _check(_lib.apo_run_device(prob.handle, C.byref(params), _stream(stream), _dptr(d_best_x), _dptr(d_best_f),
+                               _dptr(d_curve)), "apo_run_device")
+
+
+def apo_run_batch(probs, params, d_best_x, x_stride, d_best_f, d_curves=None, curve_stride=0, stream=None):
+    n = len(probs)
+    handles = (_P * n)(*[p.handle for p in probs])
+    prm = (apo_params * n)(*params)
+    _check(_lib.apo_run_batch(handles, prm, n, _stream(stream), _dptr(d_best_x), int(x_stride), _dptr(d_best_f),
+                              _dptr(d_curves), int(curve_stride)), "apo_run_batch")
+
+
+def apo_step(prob: Problem, params: apo_params, it: int, d_X, d_F, stream=None):
+    _check(_lib.apo_step(prob.handle, C.byref(params), int(it), _stream(stream), _dptr(d_X), _dptr(d_F)),
+           "apo_step")
+
+
+def apo_evaluate(prob: Problem, d_X, d_F, stream=None):
+    _check(_lib.apo_evaluate(prob.handle, _stream(stream), _dptr(d_X), int(d_X.shape[0]), _dptr(d_F)),
+           "apo_evaluate")
+
+
+def apo_clamp_eval_select(prob: Problem, d_X, d_F, d_Xnew, d_Fnew, stream=None):
+    _check(_lib.apo_clamp_eval_select(prob.handle, _stream(stream), int(d_X.shape[0]), _dptr(d_X), _dptr(d_F),
+                                      _dptr(d_Xnew), _dptr(d_Fnew)), "apo_clamp_eval_select")
+
+
+def apo_histogram_u8(d_pixels, n_per_image, n_images, d_hist, stream=None):
+    _check(_lib.apo_histogram_u8(_dptr(d_pixels), int(n_per_image), int(n_images), _dptr(d_hist),
+                                 _stream(stream)), "apo_histogram_u8")
+
+
+def apo_philox4x32_10(d_ctr, key0, key1, d_out, stream=None):
+    _check(_lib.apo_philox4x32_10(_dptr(d_ctr), int(key0) & 0xFFFFFFFF, int(key1) & 0xFFFFFFFF,
+                                  int(d_ctr.numel() // 4), _dptr(d_out), _stream(stream)), "apo_philox4x32_10")
+
+
+def raw_lib():
+    """The loaded ctypes library (for callers that time the raw C entry points)."""
+    return _lib

@@ -1,0 +1,298 @@
+// apo_device.cuh -- device-side building blocks of the APO population update
+// (cuAPO paper, Sec. 3 Eq. 1-13, Algorithm 1): the counter-based random
+// stream, order-preserving fitness keys, shared-memory bitonic sort, warp
+// subset selection (randperm), the grid barrier, and the run descriptor that
+// the host fills in.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace apo {
+
+constexpr int kThreads = 256;     // threads per CTA of every APO kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kChunk = 32;        // candidate rows evaluated together
+constexpr int kMaxComp = 10;      // composition components
+
+// Counter slots of the Philox stream: counter = (iter, p, d, slot).
+constexpr uint32_t kSlotInit = 1;   // per (p, dim pair): initial population
+constexpr uint32_t kSlotPF = 2;     // global: rand of Eq. 11
+constexpr uint32_t kSlotDR = 3;     // per 4 ranks: Dr_index keys
+constexpr uint32_t kSlotScal = 4;   // per rank: mode rand, f rand, sign, reproduction rand
+constexpr uint32_t kSlotScal2 = 5;  // per rank: M_r count rand, index j
+constexpr uint32_t kSlotPair = 6;   // per (rank, pair): k-, k+
+constexpr uint32_t kSlotDim = 7;    // per (rank, dim pair): Rand_d, mask key
+constexpr uint32_t kAll = 0xFFFFFFFFu;
+
+enum Mode : int { kDormancy = 0, kReproduction = 1, kAutotrophic = 2, kHeterotrophic = 3 };
+enum Kind : int { kSphere = 0, kElliptic = 1, kRosenbrock = 2, kRastrigin = 3, kHybrid = 4,
+                  kComposition = 5, kOtsu = 6 };
+
+// Run flags.
+constexpr int kFlagInit = 1;      // initialise the population (t = 0)
+constexpr int kFlagStepOut = 2;   // write the rank-ordered state to X_out / F_out
+
+// One shifted-rotated component: z = M (x - o), then a segmented form:
+// [0, s1) elliptic with weights ew, [s1, s2) Rosenbrock chain, [s2, D) Rastrigin.
+struct DevComp {
+    const float* o;      // [Dp]
+    const float* MT;     // [Dp][Dp] transposed rotation, zero padded; nullptr = identity
+    const float* ew;     // [Dp] elliptic weights of the first segment
+    int s1, s2;
+    float inv_2Dsig2;    // 1 / (2 D sigma^2) (composition)
+    float bias;          // composition bias
+};
+
+struct DevProblem {
+    int D, Dp, kind, ncomp;
+    const float* lb;     // [Dp]
+    const float* ub;     // [Dp]
+    DevComp comp[kMaxComp];
+    const long long* P0; // Otsu: prefix pixel counts [256]
+    const long long* P1; // Otsu: prefix first moments [256]
+};
+
+// Shared-memory carve-up of one run (byte offsets into dynamic shared memory).
+struct SmemPlan {
+    int ps_pad;          // power of two >= ps
+    int resident;        // population lives in shared memory
+    int mt_smem;         // rotation of component 0 lives in shared memory
+    uint32_t X0, X1, F0, F1, perm0, perm1, keys, MT, o, lb, ub, ew, Xc, Yc, Zc,
+        rowF, compG, compA, P0, P1, otsu, red, total;
+};
+
+struct ApoRun {
+    DevProblem prob;
+    SmemPlan plan;
+    int ps, np, T, pdr_form;
+    double pf_max;
+    uint32_t seed, run;
+    int t_begin, t_end;  // iterations executed by this launch
+    int flags;
+    int g;               // CTAs cooperating on this run (grid mode)
+    const uint32_t* thr_dr;  // [ps]    ceil(p_dr(i) 2^24)
+    const uint32_t* thr_ah;  // [T+1]   ceil(p_ah(t) 2^24)
+    const float* fsc;        // [T+1]   1 + cos(pi t / T)
+    const float* nsc;        // [T+1]   1 - t / T
+    const uint32_t* drmask;  // [T+1][ceil(ps/32)] Dr_index bitmask per iteration
+    float* X[2];             // [ps][Dp] global state buffers (non-resident / step mode)
+    void* F[2];              // [ps] FitT
+    float* X_out;            // step mode: [ps][D] rank-ordered output
+    void* F_out;
+    float* best_x;           // [D]
+    double* best_f;          // [1]
+    float* curve;            // [T+1] or nullptr
+    unsigned* bar;           // grid barrier words {count, generation, abort}
+};
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): per round two 32x32
+// multiplications, the high halves XORed with the other counter words and
+// the round key; the key advances by the Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// Draw contract: U = ((r >> 8) + 1) 2^-24 in (0, 1] (exact in binary32),
+// index = (r n) >> 32, sign = r & 1 ? -1 : +1.
+__device__ __forceinline__ float u01(uint32_t r) { return (float)((r >> 8) + 1u) * 5.9604644775390625e-8f; }
+__device__ __forceinline__ uint32_t m24p1(uint32_t r) { return (r >> 8) + 1u; }
+__device__ __forceinline__ uint32_t idx_draw(uint32_t r, uint32_t n) { return __umulhi(r, n); }
+__device__ __forceinline__ float sign_draw(uint32_t r) { return (r & 1u) ? -1.f : 1.f; }
+
+// ------------------------------------------------------- fitness ordering
+__device__ __forceinline__ uint32_t ord_key(float f)
+{
+    if (f == 0.f) f = 0.f;  // -0 sorts with +0
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ unsigned long long ord_key(double f)
+{
+    if (f == 0.0) f = 0.0;
+    const unsigned long long u = (unsigned long long)__double_as_longlong(f);
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// Sort keys: (fitness order, previous rank).  float fitness packs into 64 bits.
+template <typename FitT> struct KeyOf;
+template <> struct KeyOf<float> {
+    using T = unsigned long long;
+    __device__ static T make(float f, uint32_t r) { return ((T)ord_key(f) << 32) | r; }
+    __device__ static T pad() { return ~0ull; }
+    __device__ static uint32_t idx(T k) { return (uint32_t)k; }
+    __device__ static bool less(T a, T b) { return a < b; }
+};
+template <> struct KeyOf<double> {
+    using T = ulonglong2;
+    __device__ static T make(double f, uint32_t r) { return make_ulonglong2(ord_key(f), r); }
+    __device__ static T pad() { return make_ulonglong2(~0ull, ~0ull); }
+    __device__ static uint32_t idx(T k) { return (uint32_t)k.y; }
+    __device__ static bool less(T a, T b) { return a.x < b.x || (a.x == b.x && a.y < b.y); }
+};
+
+// Ascending bitonic sort of n (power of two) keys in shared memory by the
+// whole CTA.  Ends with a __syncthreads().
+template <typename KO>
+__device__ void bitonic_sort(typename KO::T* keys, int n)
+{
+    for (int k = 2; k <= n; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < (n >> 1); i += blockDim.x) {
+                const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+                const int hi = lo + j;
+                const bool up = (lo & k) == 0;
+                const typename KO::T a = keys[lo], b = keys[hi];
+                if (KO::less(b, a) == up) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ----------------------------------------------------- warp reductions
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// randperm(D, k) of Eq. 3 / Eq. 5: the k smallest (key, dim) pairs over the
+// warp.  Lane L holds dims d = 2 (L + 32 j) + e, j < QPL, e in {0, 1}, at
+// slot 2 j + e of `key`; `valid` marks dims < D.  Returns the lane's bitmask
+// of selected slots.  Bitwise descent on the key from the top bit, counting
+// with warp reductions, stops once the remaining candidates are all taken;
+// exact key ties fall back to the lowest dims.
+template <int QPL>
+__device__ uint32_t warp_kselect(const uint32_t (&key)[2 * QPL], uint32_t valid, int k)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t cand = valid, sel = 0;
+    int kk = k;
+    if (kk <= 0) return 0;
+    int ncand = __reduce_add_sync(0xffffffffu, __popc(cand));
+    if (kk >= ncand) return cand;
+    for (int b = 31; b >= 0; --b) {
+        uint32_t zero = 0;
+#pragma unroll
+        for (int e = 0; e < 2 * QPL; ++e)
+            if (((cand >> e) & 1u) && !((key[e] >> b) & 1u)) zero |= 1u << e;
+        const int c0 = __reduce_add_sync(0xffffffffu, __popc(zero));
+        if (kk <= c0) {
+            cand = zero;
+            ncand = c0;
+        } else {
+            sel |= zero;
+            kk -= c0;
+            cand &= ~zero;
+            ncand -= c0;
+        }
+        if (ncand == kk) return sel | cand;
+    }
+    // cand: equal keys; take the kk lowest dims, ordered by (j, lane, e).
+    int before = 0;
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const uint32_t b0 = __ballot_sync(0xffffffffu, (cand >> (2 * j)) & 1u);
+        const uint32_t b1 = __ballot_sync(0xffffffffu, (cand >> (2 * j + 1)) & 1u);
+        const uint32_t lt = (1u << lane) - 1u;
+        const int mine0 = before + __popc(b0 & lt) + __popc(b1 & lt);
+        if (((cand >> (2 * j)) & 1u) && mine0 < kk) sel |= 1u << (2 * j);
+        const int mine1 = mine0 + (int)((cand >> (2 * j)) & 1u);
+        if (((cand >> (2 * j + 1)) & 1u) && mine1 < kk) sel |= 1u << (2 * j + 1);
+        before += __popc(b0) + __popc(b1);
+    }
+    return sel;
+}
+
+// ----------------------------------------------------------- barriers
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Records the first error of the process-wide device status word.
+__device__ __forceinline__ void set_status(int* status, int code)
+{
+    atomicCAS(status, 0, code);
+}
+
+constexpr unsigned long long kBarrierTimeoutNs = 4000000000ull;  // 4 s per wait
+
+// Barrier over the g CTAs of one run.  Returns false (for every thread of the
+// CTA) when the run was aborted or the wait timed out; the caller then stops
+// the run.  `gen` is the CTA's count of barriers passed.
+__device__ __noinline__ static bool run_barrier(unsigned* bar, int g, unsigned& gen, int* status, int* s_flag)
+{
+    __syncthreads();
+    if (g > 1) {
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            __threadfence();
+            const unsigned arrived = atomicAdd(&bar[0], 1u);
+            if (arrived == (unsigned)g - 1u) {
+                atomicExch(&bar[0], 0u);
+                __threadfence();
+                atomicAdd(&bar[1], 1u);
+            } else {
+                const unsigned long long t0 = global_ns();
+                while (ld_acquire(&bar[1]) == gen) {
+                    if (ld_acquire(&bar[2]) != 0u) { ok = 0; break; }
+                    if (global_ns() - t0 > kBarrierTimeoutNs) {
+                        set_status(status, 4 /* APO_ERR_TIMEOUT */);
+                        atomicExch(&bar[2], 1u);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            if (ld_acquire(&bar[2]) != 0u) ok = 0;
+            ++gen;
+            __threadfence();
+            *s_flag = ok;
+        }
+        __syncthreads();
+        return *s_flag != 0;
+    }
+    return true;
+}
+
+}  // namespace apo

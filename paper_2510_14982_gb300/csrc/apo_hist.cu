@@ -1,0 +1,100 @@
+// apo_hist.cu -- 256-bin histograms of 8-bit images and the Otsu prefix
+// tables (the thresholding application of the cuAPO paper, Sec. 5.2).
+//
+// The histogram is HBM-bound: every pixel byte is read once with 16-byte
+// vector loads and counted into per-warp shared-memory sub-histograms, which
+// are merged into the image's global int32 bins with one atomic per bin and
+// CTA.  Integer counting makes the result independent of the order of
+// accumulation (bit-exact).
+#include "apo_internal.h"
+
+namespace apo {
+
+constexpr int kHistThreads = 512;
+constexpr int kHistWarps = kHistThreads / 32;
+
+__global__ void __launch_bounds__(kHistThreads) histogram_u8_kernel(const uint8_t* __restrict__ px,
+                                                                    long long n_per_image,
+                                                                    long long chunk, int32_t* hist)
+{
+    __shared__ unsigned sub[kHistWarps][256];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < kHistWarps * 256; i += kHistThreads) (&sub[0][0])[i] = 0;
+    __syncthreads();
+
+    const int image = blockIdx.y;
+    const long long begin = (long long)blockIdx.x * chunk;
+    long long end = begin + chunk;
+    if (end > n_per_image) end = n_per_image;
+    const uint8_t* base = px + (size_t)image * (size_t)n_per_image;
+    unsigned* h = sub[warp];
+
+    // bytes before the first 16-byte boundary and after the last one
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(base + begin);
+    long long head = (long long)((16 - (addr & 15)) & 15);
+    if (head > end - begin) head = end - begin;
+    for (long long i = begin + tid; i < begin + head; i += kHistThreads) atomicAdd(&h[base[i]], 1u);
+    const long long vbeg = begin + head;
+    const long long nvec = (end - vbeg) >> 4;
+    const uint4* v = reinterpret_cast<const uint4*>(base + vbeg);
+    for (long long i = tid; i < nvec; i += kHistThreads) {
+        const uint4 w = __ldcs(v + i);
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            atomicAdd(&h[words[k] & 255u], 1u);
+            atomicAdd(&h[(words[k] >> 8) & 255u], 1u);
+            atomicAdd(&h[(words[k] >> 16) & 255u], 1u);
+            atomicAdd(&h[words[k] >> 24], 1u);
+        }
+    }
+    for (long long i = vbeg + (nvec << 4) + tid; i < end; i += kHistThreads) atomicAdd(&h[base[i]], 1u);
+    __syncthreads();
+    for (int b = tid; b < 256; b += kHistThreads) {
+        unsigned s = 0;
+#pragma unroll
+        for (int w = 0; w < kHistWarps; ++w) s += sub[w][b];
+        if (s) atomicAdd(reinterpret_cast<unsigned*>(hist + (size_t)image * 256 + b), s);
+    }
+}
+
+cudaError_t launch_histogram_u8(const uint8_t* d_px, int64_t n_per_image, int n_images, int32_t* d_hist,
+                                cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(d_hist, 0, sizeof(int32_t) * 256 * (size_t)n_images, st);
+    if (e != cudaSuccess || n_per_image == 0 || n_images == 0) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // about four CTAs per SM over the whole batch, each a 16-byte multiple
+    long long total = n_per_image * (long long)n_images;
+    long long chunk = total / ((long long)sms * 4);
+    if (chunk < 65536) chunk = 65536;
+    chunk = (chunk + 15) & ~15ll;
+    long long per_image = (n_per_image + chunk - 1) / chunk;
+    dim3 grid((unsigned)per_image, (unsigned)n_images);
+    histogram_u8_kernel<<<grid, kHistThreads, 0, st>>>(d_px, n_per_image, chunk, d_hist);
+    return cudaGetLastError();
+}
+
+// P0[v] = sum_{i<=v} h[i], P1[v] = sum_{i<=v} i h[i] (int64, exact).
+__global__ void otsu_prefix_kernel(const int32_t* __restrict__ h, long long* P0, long long* P1)
+{
+    if (threadIdx.x == 0) {
+        long long a = 0, b = 0;
+        for (int v = 0; v < 256; ++v) {
+            a += (long long)h[v];
+            b += (long long)v * (long long)h[v];
+            P0[v] = a;
+            P1[v] = b;
+        }
+    }
+}
+
+cudaError_t launch_otsu_prefix(const int32_t* d_hist, long long* d_P0, long long* d_P1, cudaStream_t st)
+{
+    otsu_prefix_kernel<<<1, 32, 0, st>>>(d_hist, d_P0, d_P1);
+    return cudaGetLastError();
+}
+
+}  // namespace apo

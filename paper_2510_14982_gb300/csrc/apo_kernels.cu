@@ -1,0 +1,891 @@
+// apo_kernels.cu -- the APO population update on the GPU (cuAPO paper,
+// Sec. 3 Eq. 1-13 and Algorithm 1).
+//
+// One CTA (resident mode) or a group of g cooperating CTAs (grid mode) runs
+// the whole device-side iteration loop of one optimisation run:
+//   sort (F, previous rank) -> [Dr_index, precomputed by dr_kernel]
+//   -> candidate generation, one warp per protozoon (Eq. 1-10, 12-13)
+//   -> bound clamp -> evaluation (z = M (x - o) as a shared-memory tile GEMM,
+//      then the objective epilogue) -> greedy replacement -> barrier.
+// In resident mode the population, its fitness and the rotation live in
+// shared memory; in grid mode the population lives in global memory (L2) and
+// is double buffered so that every candidate reads the start-of-iteration
+// snapshot, as the synchronous "parallel for" of Algorithm 1 requires.
+#include <cstdio>
+
+#include "apo_device.cuh"
+#include "apo_internal.h"
+
+namespace apo {
+
+constexpr float kEps = 2.220446049250313e-16f;  // eps of Eq. 7 and Eq. 10 (2^-52)
+
+// ------------------------------------------------------------- Dr_index
+// Eq. 11 and Algorithm 1: pf = pf_max * rand, m = ceil(ps * pf) (float64),
+// Dr_index = the m smallest (Philox key, rank) pairs.  One CTA per (run, t);
+// an exact radix select over 8-bit digits of the 32-bit keys.
+__global__ void __launch_bounds__(kThreads) dr_kernel(const ApoRun* __restrict__ runs,
+                                                      const int* __restrict__ offs, int n_runs,
+                                                      int n_work)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    uint32_t* keys = reinterpret_cast<uint32_t*>(dyn);
+    __shared__ unsigned hist[256];
+    __shared__ unsigned s_prefix, s_need, s_eq;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+        int lo = 0, hi = n_runs - 1;  // run k with offs[k] <= w < offs[k+1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (offs[mid] <= w) lo = mid; else hi = mid - 1;
+        }
+        const ApoRun& R = runs[lo];
+        const int t = R.t_begin + (w - offs[lo]);
+        const int ps = R.ps;
+        const int W = (ps + 31) >> 5;
+        uint32_t* out = const_cast<uint32_t*>(R.drmask) + (size_t)t * W;
+
+        const uint4 pw = philox((uint32_t)t, kAll, kAll, kSlotPF, R.seed, R.run);
+        const double u = (double)m24p1(pw.x) * 5.9604644775390625e-8;
+        const double pf = R.pf_max * u;
+        const int m = (int)ceil((double)ps * pf);
+
+        for (int q = tid; q < ((ps + 3) >> 2); q += blockDim.x) {
+            const uint4 k4 = philox((uint32_t)t, (uint32_t)q, kAll, kSlotDR, R.seed, R.run);
+            const uint32_t kv[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (4 * q + e < ps) keys[4 * q + e] = kv[e];
+        }
+        __syncthreads();
+
+        uint32_t K = 0;
+        unsigned need = (unsigned)m, eq = 0;
+        if (m > 0 && m < ps) {
+            uint32_t prefix = 0, pmask = 0;
+            for (int pass = 0; pass < 4; ++pass) {
+                const int shift = 24 - 8 * pass;
+                for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
+                __syncthreads();
+                for (int r = tid; r < ps; r += blockDim.x) {
+                    const uint32_t k = keys[r];
+                    if ((k & pmask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    unsigned s = 0;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) s += hist[8 * lane + i];
+                    unsigned incl = s;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const unsigned ballot = __ballot_sync(0xffffffffu, incl >= need);
+                    const int L = __ffs(ballot) - 1;
+                    if (lane == L) {
+                        unsigned cum = incl - s;
+                        int digit = 8 * lane;
+                        for (int i = 0; i < 8; ++i) {
+                            if (cum + hist[8 * lane + i] >= need) { digit = 8 * lane + i; break; }
+                            cum += hist[8 * lane + i];
+                        }
+                        s_prefix = prefix | ((uint32_t)digit << shift);
+                        s_need = need - cum;
+                        s_eq = hist[digit];
+                    }
+                }
+                __syncthreads();
+                prefix = s_prefix;
+                pmask |= 255u << shift;
+                need = s_need;
+                eq = s_eq;
+                __syncthreads();
+            }
+            K = prefix;
+        }
+        for (int base = warp * 32; base < W * 32; base += blockDim.x) {
+            const int r = base + lane;
+            bool sel = false;
+            if (r < ps) {
+                if (m >= ps) sel = true;
+                else if (m > 0) {
+                    const uint32_t k = keys[r];
+                    if (k < K) sel = true;
+                    else if (k == K) {
+                        if (need >= eq) sel = true;
+                        else {  // exact key ties: the lowest ranks first
+                            unsigned before = 0;
+                            for (int r2 = 0; r2 < r; ++r2) before += (keys[r2] == K);
+                            sel = before < need;
+                        }
+                    }
+                }
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, sel);
+            if (lane == 0) out[base >> 5] = b;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------- shared layout
+template <typename FitT>
+struct Smem {
+    float* X[2];
+    FitT* F[2];
+    uint32_t* perm[2];
+    void* keys;
+    float* MT;
+    float *o, *lb, *ub, *ew;
+    float *Xc, *Yc, *Zc;
+    FitT* rowF;
+    float *compG, *compA;
+    long long *P0, *P1;
+    int* otsu;
+    void* red;
+};
+
+template <typename FitT>
+__device__ __forceinline__ Smem<FitT> carve(unsigned char* base, const SmemPlan& L)
+{
+    Smem<FitT> S;
+    S.X[0] = reinterpret_cast<float*>(base + L.X0);
+    S.X[1] = reinterpret_cast<float*>(base + L.X1);
+    S.F[0] = reinterpret_cast<FitT*>(base + L.F0);
+    S.F[1] = reinterpret_cast<FitT*>(base + L.F1);
+    S.perm[0] = reinterpret_cast<uint32_t*>(base + L.perm0);
+    S.perm[1] = reinterpret_cast<uint32_t*>(base + L.perm1);
+    S.keys = base + L.keys;
+    S.MT = reinterpret_cast<float*>(base + L.MT);
+    S.o = reinterpret_cast<float*>(base + L.o);
+    S.lb = reinterpret_cast<float*>(base + L.lb);
+    S.ub = reinterpret_cast<float*>(base + L.ub);
+    S.ew = reinterpret_cast<float*>(base + L.ew);
+    S.Xc = reinterpret_cast<float*>(base + L.Xc);
+    S.Yc = reinterpret_cast<float*>(base + L.Yc);
+    S.Zc = reinterpret_cast<float*>(base + L.Zc);
+    S.rowF = reinterpret_cast<FitT*>(base + L.rowF);
+    S.compG = reinterpret_cast<float*>(base + L.compG);
+    S.compA = reinterpret_cast<float*>(base + L.compA);
+    S.P0 = reinterpret_cast<long long*>(base + L.P0);
+    S.P1 = reinterpret_cast<long long*>(base + L.P1);
+    S.otsu = reinterpret_cast<int*>(base + L.otsu);
+    S.red = base + L.red;
+    return S;
+}
+
+// Loads the run's constant vectors (and the rotation of a single-component
+// objective when it fits) into shared memory.
+template <typename FitT>
+__device__ void load_constants(const ApoRun& R, const Smem<FitT>& S)
+{
+    const DevProblem& P = R.prob;
+    const int Dp = P.Dp;
+    const DevComp& C = P.comp[0];
+    for (int i = threadIdx.x; i < Dp; i += blockDim.x) {
+        S.lb[i] = P.lb[i];
+        S.ub[i] = P.ub[i];
+        S.o[i] = C.o ? C.o[i] : 0.f;
+        S.ew[i] = C.ew ? C.ew[i] : 1.f;
+    }
+    if (R.plan.mt_smem && C.MT) {
+        const float4* src = reinterpret_cast<const float4*>(C.MT);
+        float4* dst = reinterpret_cast<float4*>(S.MT);
+        for (int i = threadIdx.x; i < Dp * Dp / 4; i += blockDim.x) dst[i] = src[i];
+    }
+    if (P.kind == kOtsu) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+            S.P0[i] = P.P0[i];
+            S.P1[i] = P.P1[i];
+        }
+    }
+}
+
+// ------------------------------------------------------------ evaluation
+// Zc[rows][Dp] = Yc[rows][Dp] * MT[Dp][Dp] (both zero padded beyond D):
+// FP32 FMA with 4 x 4 register tiles over the CTA.
+__device__ void tile_gemm(const float* __restrict__ Y, const float* __restrict__ MT,
+                          float* __restrict__ Z, int rows, int Dp)
+{
+    const int ct = Dp >> 2;
+    const int rt = (rows + 3) >> 2;
+    for (int tile = threadIdx.x; tile < rt * ct; tile += blockDim.x) {
+        const int tr = tile / ct, tc = tile - tr * ct;
+        const float* y0 = Y + (size_t)(4 * tr) * Dp;
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        for (int k = 0; k < Dp; k += 4) {
+            float4 a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(y0 + (size_t)i * Dp + k);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                b[kk] = *reinterpret_cast<const float4*>(MT + (size_t)(k + kk) * Dp + 4 * tc);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float av[4] = {a[i].x, a[i].y, a[i].z, a[i].w};
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    acc[i][0] = fmaf(av[kk], b[kk].x, acc[i][0]);
+                    acc[i][1] = fmaf(av[kk], b[kk].y, acc[i][1]);
+                    acc[i][2] = fmaf(av[kk], b[kk].z, acc[i][2]);
+                    acc[i][3] = fmaf(av[kk], b[kk].w, acc[i][3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            *reinterpret_cast<float4*>(Z + (size_t)(4 * tr + i) * Dp + 4 * tc) =
+                make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    }
+}
+
+// Segmented objective of one row by one warp: [0, s1) high-conditioned
+// elliptic, [s1, s2) chained Rosenbrock, [s2, D) Rastrigin cosine sum.
+__device__ float seg_value(const float* z, const DevComp& C, const float* ew, int D)
+{
+    const int lane = threadIdx.x & 31;
+    float s = 0.f;
+    for (int d = lane; d < D; d += 32) {
+        const float v = z[d];
+        if (d < C.s1) {
+            s = fmaf(ew[d] * v, v, s);
+        } else if (d < C.s2) {
+            if (d + 1 < C.s2) {
+                const float a = z[d + 1] - v * v;
+                const float b = v - 1.f;
+                s += 100.f * a * a + b * b;
+            }
+        } else {
+            s += v * v - 10.f * cospif(2.f * v) + 10.f;
+        }
+    }
+    return warp_sum(s);
+}
+
+// Otsu between-class variance of one row by one warp (thresholds in lanes
+// 0..T-1), negated.  The float64 operations follow a fixed order with
+// explicit round-to-nearest intrinsics (no contraction) so that the value is
+// reproducible bit for bit.
+__device__ double otsu_row(const float* x, int T, const long long* P0, const long long* P1,
+                           int* scratch)
+{
+    const int lane = threadIdx.x & 31;
+    int tv = 0;
+    if (lane < T) {
+        float f = floorf(x[lane]);
+        f = fminf(fmaxf(f, 0.f), 255.f);
+        tv = (int)f;
+    }
+    int rank = 0;
+    for (int i = 0; i < T; ++i) {
+        const int ti = __shfl_sync(0xffffffffu, tv, i);
+        if (ti < tv || (ti == tv && i < lane)) ++rank;
+    }
+    __syncwarp();
+    if (lane < T) scratch[rank] = tv;
+    __syncwarp();
+    double sigma = 0.0;
+    if (lane == 0) {
+        const long long N = P0[255], Ssum = P1[255];
+        const double muT = __ddiv_rn((double)Ssum, (double)N);
+        int prev = -1;
+        for (int c = 0; c <= T; ++c) {
+            const int hi = (c < T) ? scratch[c] : 255;
+            long long nc = 0, sc = 0;
+            if (hi > prev) {
+                nc = P0[hi] - (prev >= 0 ? P0[prev] : 0ll);
+                sc = P1[hi] - (prev >= 0 ? P1[prev] : 0ll);
+                prev = hi;
+            }
+            if (nc > 0) {
+                const double omega = __ddiv_rn((double)nc, (double)N);
+                const double mu = __ddiv_rn((double)sc, (double)nc);
+                const double dm = __dsub_rn(mu, muT);
+                double term = __dmul_rn(omega, dm);
+                term = __dmul_rn(term, dm);
+                sigma = __dadd_rn(sigma, term);
+            }
+        }
+    }
+    sigma = __shfl_sync(0xffffffffu, sigma, 0);
+    __syncwarp();
+    return -sigma;
+}
+
+// Evaluates the candidate rows Xc[0, rows) into rowF.  Called by the whole
+// CTA; ends synchronised.
+template <typename FitT>
+__device__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S, int rows)
+{
+    const DevProblem& P = R.prob;
+    const int D = P.D, Dp = P.Dp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (P.kind == kOtsu) {
+        for (int row = warp; row < rows; row += kWarps) {
+            const double f = otsu_row(S.Xc + (size_t)row * Dp, D, S.P0, S.P1, S.otsu + warp * 32);
+            if (lane == 0) S.rowF[row] = (FitT)f;
+        }
+        __syncthreads();
+        return;
+    }
+    for (int c = 0; c < P.ncomp; ++c) {
+        const DevComp& C = P.comp[c];
+        const float* o = (c == 0) ? S.o : C.o;
+        for (int i = threadIdx.x; i < rows * Dp; i += blockDim.x) {
+            const int d = i % Dp;
+            S.Yc[i] = d < D ? S.Xc[i] - o[d] : 0.f;
+        }
+        __syncthreads();
+        const float* Z = S.Yc;
+        if (C.MT) {
+            const float* MT = (c == 0 && R.plan.mt_smem) ? S.MT : C.MT;
+            tile_gemm(S.Yc, MT, S.Zc, rows, Dp);
+            Z = S.Zc;
+            __syncthreads();
+        }
+        const float* ew = (c == 0) ? S.ew : C.ew;
+        for (int row = warp; row < rows; row += kWarps) {
+            const float v = seg_value(Z + (size_t)row * Dp, C, ew, D);
+            if (P.ncomp == 1) {
+                if (lane == 0) S.rowF[row] = (FitT)v;
+            } else {
+                float d2 = 0.f;
+                for (int d = lane; d < D; d += 32) {
+                    const float y = S.Yc[(size_t)row * Dp + d];
+                    d2 = fmaf(y, y, d2);
+                }
+                d2 = warp_sum(d2);
+                if (lane == 0) {
+                    S.compG[row * kMaxComp + c] = v;
+                    S.compA[row * kMaxComp + c] = -d2 * C.inv_2Dsig2;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (P.ncomp > 1) {
+        // f = sum_k w_k (g_k + bias_k) / sum_k w_k, w_k = exp(a_k - max a).
+        for (int row = warp; row < rows; row += kWarps) {
+            const bool on = lane < P.ncomp;
+            const float a = on ? S.compA[row * kMaxComp + lane] : -INFINITY;
+            const float amax = warp_max(a);
+            const float w = on ? expf(a - amax) : 0.f;
+            const float gv = on ? S.compG[row * kMaxComp + lane] + P.comp[lane < kMaxComp ? lane : 0].bias : 0.f;
+            const float num = warp_sum(w * gv);
+            const float den = warp_sum(w);
+            if (lane == 0) S.rowF[row] = (FitT)(num / den);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------- state access
+template <typename T>
+__device__ __forceinline__ T ldst(const T* p, bool resident)
+{
+    return resident ? *p : __ldcg(p);
+}
+
+// ------------------------------------------------- candidate generation
+// Population initialisation (Algorithm 1): X_p = Xmin + U (Xmax - Xmin).
+template <typename FitT, int QPL>
+__device__ void gen_init_row(const ApoRun& R, const Smem<FitT>& S, int p, int row)
+{
+    const int lane = threadIdx.x & 31;
+    const int D = R.prob.D, Dp = R.prob.Dp;
+    float* xc = S.Xc + (size_t)row * Dp;
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const int q = lane + 32 * j;
+        const int d0 = 2 * q;
+        if (d0 < D) {
+            const uint4 w = philox(0u, (uint32_t)p, (uint32_t)q, kSlotInit, R.seed, R.run);
+            xc[d0] = fmaf(u01(w.x), S.ub[d0] - S.lb[d0], S.lb[d0]);
+            if (d0 + 1 < D) xc[d0 + 1] = fmaf(u01(w.z), S.ub[d0 + 1] - S.lb[d0 + 1], S.lb[d0 + 1]);
+            else if (d0 + 1 < Dp) xc[d0 + 1] = 0.f;
+        } else if (d0 < Dp) {
+            xc[d0] = 0.f;
+            xc[d0 + 1] = 0.f;
+        }
+    }
+}
+
+// One candidate (rank r, 0-based) by one warp: mode selection (Eq. 12-13,
+// Algorithm 1), masks (Eq. 3, Eq. 5), dormancy (Eq. 1), reproduction
+// (Eq. 2), autotrophic (Eq. 6-7) or heterotrophic (Eq. 8-10) foraging, then
+// the bound clamp.  Writes row `row` of Xc.
+template <typename FitT, int QPL>
+__device__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* __restrict__ X,
+                             const FitT* __restrict__ F, const uint32_t* perm, bool res, int t,
+                             int r, int row)
+{
+    const int lane = threadIdx.x & 31;
+    const int D = R.prob.D, Dp = R.prob.Dp, ps = R.ps;
+    const uint32_t seed = R.seed, run = R.run;
+    const uint4 sc = philox((uint32_t)t, (uint32_t)r, kAll, kSlotScal, seed, run);
+    const uint4 sc2 = philox((uint32_t)t, (uint32_t)r, kAll, kSlotScal2, seed, run);
+    const int W = (ps + 31) >> 5;
+    const bool in_dr = (R.drmask[(size_t)t * W + (r >> 5)] >> (r & 31)) & 1u;
+    const uint32_t mm = m24p1(sc.x);
+    int mode;
+    if (in_dr) mode = (mm < R.thr_dr[r]) ? kDormancy : kReproduction;
+    else mode = (mm < R.thr_ah[t]) ? kAutotrophic : kHeterotrophic;
+
+    uint32_t A[2 * QPL], B[2 * QPL];
+    uint32_t valid = 0;
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const int q = lane + 32 * j;
+        if (2 * q < D) {
+            const uint4 w = philox((uint32_t)t, (uint32_t)r, (uint32_t)q, kSlotDim, seed, run);
+            A[2 * j] = w.x; B[2 * j] = w.y; A[2 * j + 1] = w.z; B[2 * j + 1] = w.w;
+            valid |= 1u << (2 * j);
+            if (2 * q + 1 < D) valid |= 1u << (2 * j + 1);
+        } else {
+            A[2 * j] = B[2 * j] = A[2 * j + 1] = B[2 * j + 1] = 0u;
+        }
+    }
+    uint32_t mask = 0;
+    if (mode == kReproduction) {
+        const int k = (int)(((unsigned long long)D * m24p1(sc2.x) + 0xFFFFFFull) >> 24);
+        mask = warp_kselect<QPL>(B, valid, k);
+    } else if (mode != kDormancy) {
+        const int k = (D * (r + 1) + ps - 1) / ps;
+        mask = warp_kselect<QPL>(B, valid, k);
+    }
+
+    // rows gathered from the snapshot
+    const int si = (int)perm[r];
+    float xi[2 * QPL], xa[2 * QPL], acc[2 * QPL];
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const int q = lane + 32 * j;
+        float2 v = make_float2(0.f, 0.f);
+        if (2 * q < D) v = ldst(reinterpret_cast<const float2*>(X + (size_t)si * Dp) + q, res);
+        xi[2 * j] = v.x;
+        xi[2 * j + 1] = v.y;
+        acc[2 * j] = acc[2 * j + 1] = 0.f;
+        xa[2 * j] = xa[2 * j + 1] = 0.f;
+    }
+    const float inv_np = 1.f / (float)R.np;
+    float ff = 0.f, s = 1.f;
+    if (mode == kAutotrophic || mode == kHeterotrophic) {
+        ff = u01(sc.y) * R.fsc[t];
+        for (int k = 1; k <= R.np; ++k) {
+            int a, b;
+            if (mode == kAutotrophic) {
+                const uint4 pr = philox((uint32_t)t, (uint32_t)r, (uint32_t)(k - 1), kSlotPair, seed, run);
+                a = (int)idx_draw(pr.x, (uint32_t)ps);
+                b = (int)idx_draw(pr.y, (uint32_t)ps);
+            } else {
+                a = r - k < 0 ? 0 : r - k;
+                b = r + k > ps - 1 ? ps - 1 : r + k;
+            }
+            const int sa = (int)perm[a], sb = (int)perm[b];
+            const float fa = (float)ldst(F + sa, res), fb = (float)ldst(F + sb, res);
+            const float w = expf(-fabsf(fa / (fb + kEps)));
+#pragma unroll
+            for (int j = 0; j < QPL; ++j) {
+                const int q = lane + 32 * j;
+                if (2 * q < D) {
+                    const float2 va = ldst(reinterpret_cast<const float2*>(X + (size_t)sa * Dp) + q, res);
+                    const float2 vb = ldst(reinterpret_cast<const float2*>(X + (size_t)sb * Dp) + q, res);
+                    acc[2 * j] = fmaf(w, va.x - vb.x, acc[2 * j]);
+                    acc[2 * j + 1] = fmaf(w, va.y - vb.y, acc[2 * j + 1]);
+                }
+            }
+        }
+        if (mode == kAutotrophic) {
+            const int jr = (int)idx_draw(sc2.y, (uint32_t)ps);
+            const int sj = (int)perm[jr];
+#pragma unroll
+            for (int j = 0; j < QPL; ++j) {
+                const int q = lane + 32 * j;
+                if (2 * q < D) {
+                    const float2 v = ldst(reinterpret_cast<const float2*>(X + (size_t)sj * Dp) + q, res);
+                    xa[2 * j] = v.x;
+                    xa[2 * j + 1] = v.y;
+                }
+            }
+        } else {
+            s = sign_draw(sc.z);
+        }
+    } else if (mode == kReproduction) {
+        s = sign_draw(sc.z);
+    }
+    const float rho = u01(sc.w);
+    const float nsc = R.nsc[t];
+
+    float* xc = S.Xc + (size_t)row * Dp;
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const int q = lane + 32 * j;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int d = 2 * q + e;
+            const int sl = 2 * j + e;
+            if (d < D) {
+                const float lb = S.lb[d], ub = S.ub[d];
+                const bool mk = (mask >> sl) & 1u;
+                const float x0 = xi[sl];
+                float x = x0;
+                if (mode == kDormancy) {
+                    x = fmaf(u01(A[sl]), ub - lb, lb);                          // Eq. 1
+                } else if (mk) {
+                    if (mode == kReproduction) {
+                        x = x0 + s * rho * fmaf(u01(A[sl]), ub - lb, lb);       // Eq. 2
+                    } else if (mode == kAutotrophic) {
+                        x = x0 + ff * (xa[sl] - x0 + acc[sl] * inv_np);         // Eq. 6
+                    } else {
+                        const float xnear = (1.f + s * u01(A[sl]) * nsc) * x0;  // Eq. 9
+                        x = x0 + ff * (xnear - x0 + acc[sl] * inv_np);          // Eq. 8
+                    }
+                }
+                xc[d] = fminf(fmaxf(x, lb), ub);
+            } else if (d < Dp) {
+                xc[d] = 0.f;
+            }
+        }
+    }
+}
+
+// -------------------------------------------------------------- the run
+template <typename FitT>
+__device__ void find_best(const Smem<FitT>& S, const FitT* F, const uint32_t* perm, int ps,
+                          bool res, typename KeyOf<FitT>::T* red, int* out_rank)
+{
+    using KO = KeyOf<FitT>;
+    typename KO::T best = KO::pad();
+    for (int r = threadIdx.x; r < ps; r += blockDim.x) {
+        const typename KO::T k = KO::make(ldst(F + perm[r], res), (uint32_t)r);
+        if (KO::less(k, best)) best = k;
+    }
+    red[threadIdx.x] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        typename KO::T b = red[0];
+        for (int i = 1; i < (int)blockDim.x; ++i)
+            if (KO::less(red[i], b)) b = red[i];
+        *out_rank = (int)KO::idx(b);
+    }
+    __syncthreads();
+}
+
+template <typename FitT, int QPL>
+__device__ void run_one(const ApoRun& R, int local, unsigned char* smem, int* status, int* s_flag,
+                        int* s_int)
+{
+    using KO = KeyOf<FitT>;
+    using KT = typename KO::T;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const DevProblem& P = R.prob;
+    const int D = P.D, Dp = P.Dp, ps = R.ps, g = R.g;
+    const SmemPlan& L = R.plan;
+    const Smem<FitT> S = carve<FitT>(smem, L);
+    const bool res = L.resident != 0;
+    unsigned bgen = 0;
+
+    load_constants<FitT>(R, S);
+    for (int r = tid; r < ps; r += blockDim.x) S.perm[0][r] = (uint32_t)r;
+    float* Xs[2];
+    FitT* Fs[2];
+    if (res) {
+        Xs[0] = S.X[0]; Xs[1] = S.X[1]; Fs[0] = S.F[0]; Fs[1] = S.F[1];
+    } else {
+        Xs[0] = R.X[0]; Xs[1] = R.X[1];
+        Fs[0] = static_cast<FitT*>(R.F[0]); Fs[1] = static_cast<FitT*>(R.F[1]);
+    }
+    const int r0 = (int)((long long)ps * local / g);
+    const int r1 = (int)((long long)ps * (local + 1) / g);
+    __syncthreads();
+
+    if (R.flags & kFlagInit) {
+        for (int c0 = r0; c0 < r1; c0 += kChunk) {
+            const int rows = min(kChunk, r1 - c0);
+            for (int row = warp; row < rows; row += kWarps) gen_init_row<FitT, QPL>(R, S, c0 + row, row);
+            __syncthreads();
+            eval_chunk<FitT>(R, S, rows);
+            for (int row = warp; row < rows; row += kWarps) {
+                float* dst = Xs[0] + (size_t)(c0 + row) * Dp;
+                for (int d = lane; d < Dp; d += 32) dst[d] = S.Xc[(size_t)row * Dp + d];
+                if (lane == 0) Fs[0][c0 + row] = S.rowF[row];
+            }
+            __syncthreads();
+        }
+    } else if (res) {
+        const float* gx = R.X[0];
+        const FitT* gf = static_cast<const FitT*>(R.F[0]);
+        for (int i = tid; i < ps * Dp; i += blockDim.x) Xs[0][i] = gx[i];
+        for (int i = tid; i < ps; i += blockDim.x) Fs[0][i] = gf[i];
+        __syncthreads();
+    }
+    if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
+
+    int cur = 0, pc = 0;
+    KT* keys = static_cast<KT*>(S.keys);
+    for (int t = R.t_begin; t <= R.t_end; ++t) {
+        // Algorithm 1: sort by fitness; ties keep the previous order.
+        const uint32_t* perm = S.perm[pc];
+        uint32_t* pnew = S.perm[pc ^ 1];
+        for (int r = tid; r < L.ps_pad; r += blockDim.x)
+            keys[r] = r < ps ? KO::make(ldst(Fs[cur] + perm[r], res), (uint32_t)r) : KO::pad();
+        __syncthreads();
+        bitonic_sort<KO>(keys, L.ps_pad);
+        for (int r = tid; r < ps; r += blockDim.x) pnew[r] = perm[KO::idx(keys[r])];
+        __syncthreads();
+        pc ^= 1;
+        perm = pnew;
+        if (local == 0 && tid == 0 && R.curve) R.curve[t - 1] = (float)ldst(Fs[cur] + perm[0], res);
+
+        for (int c0 = r0; c0 < r1; c0 += kChunk) {
+            const int rows = min(kChunk, r1 - c0);
+            for (int row = warp; row < rows; row += kWarps)
+                gen_step_row<FitT, QPL>(R, S, Xs[cur], Fs[cur], perm, res, t, c0 + row, row);
+            __syncthreads();
+            eval_chunk<FitT>(R, S, rows);
+            // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i).
+            for (int row = warp; row < rows; row += kWarps) {
+                const int slot = (int)perm[c0 + row];
+                const FitT fo = ldst(Fs[cur] + slot, res);
+                const FitT fn = S.rowF[row];
+                const bool acc = fn < fo;
+                const float4* src = acc ? reinterpret_cast<const float4*>(S.Xc + (size_t)row * Dp)
+                                        : reinterpret_cast<const float4*>(Xs[cur] + (size_t)slot * Dp);
+                float4* dst = reinterpret_cast<float4*>(Xs[cur ^ 1] + (size_t)slot * Dp);
+                for (int v = lane; v < (Dp >> 2); v += 32) dst[v] = (acc || res) ? src[v] : __ldcg(src + v);
+                if (lane == 0) Fs[cur ^ 1][slot] = acc ? fn : fo;
+            }
+            __syncthreads();
+        }
+        if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
+        cur ^= 1;
+    }
+
+    const uint32_t* perm = S.perm[pc];
+    if (R.flags & kFlagStepOut) {
+        float* xo = R.X_out;
+        FitT* fo = static_cast<FitT*>(R.F_out);
+        for (int r = r0 + warp; r < r1; r += kWarps) {
+            const int slot = (int)perm[r];
+            for (int d = lane; d < D; d += 32) xo[(size_t)r * D + d] = ldst(Xs[cur] + (size_t)slot * Dp + d, res);
+            if (lane == 0) fo[r] = ldst(Fs[cur] + slot, res);
+        }
+    } else if (local == 0) {
+        find_best<FitT>(S, Fs[cur], perm, ps, res, static_cast<KT*>(S.red), s_int);
+        const int slot = (int)perm[*s_int];
+        const FitT fb = ldst(Fs[cur] + slot, res);
+        if (tid == 0) {
+            if (R.curve) R.curve[R.t_end] = (float)fb;
+            if (R.best_f) *R.best_f = (double)fb;
+        }
+        if (R.best_x)
+            for (int d = tid; d < D; d += blockDim.x) R.best_x[d] = ldst(Xs[cur] + (size_t)slot * Dp + d, res);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void copy_run(ApoRun* dst, const ApoRun* src)
+{
+    static_assert(sizeof(ApoRun) % 8 == 0, "ApoRun must be 8-byte sized");
+    const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(ApoRun) / 8); i += blockDim.x) d[i] = s[i];
+}
+
+template <typename FitT, int QPL>
+__global__ void __launch_bounds__(kThreads) run_kernel(const ApoRun* __restrict__ runs, int n_runs,
+                                                       int grid_g, int* queue, int* status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ApoRun R;
+    __shared__ int s_run, s_flag, s_int;
+    if (grid_g > 0) {
+        const int run = blockIdx.x / grid_g, local = blockIdx.x % grid_g;
+        if (run >= n_runs) return;
+        copy_run(&R, runs + run);
+        __syncthreads();
+        run_one<FitT, QPL>(R, local, smem, status, &s_flag, &s_int);
+        return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) s_run = atomicAdd(queue, 1);
+        __syncthreads();
+        const int run = s_run;
+        if (run >= n_runs) return;
+        copy_run(&R, runs + run);
+        __syncthreads();
+        run_one<FitT, QPL>(R, 0, smem, status, &s_flag, &s_int);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------- evaluation hook
+template <typename FitT, int QPL>
+__global__ void __launch_bounds__(kThreads) eval_kernel(const ApoRun* __restrict__ run, int n,
+                                                        const float* __restrict__ X, FitT* F,
+                                                        int select, float* Xsel, FitT* Fsel)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ApoRun R;
+    copy_run(&R, run);
+    __syncthreads();
+    const Smem<FitT> S = carve<FitT>(smem, R.plan);
+    load_constants<FitT>(R, S);
+    __syncthreads();
+    const int D = R.prob.D, Dp = R.prob.Dp, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c0 = blockIdx.x * kChunk; c0 < n; c0 += gridDim.x * kChunk) {
+        const int rows = min(kChunk, n - c0);
+        for (int row = warp; row < rows; row += kWarps) {
+            for (int d = lane; d < Dp; d += 32) {
+                float x = d < D ? X[(size_t)(c0 + row) * D + d] : 0.f;
+                if (select && d < D) x = fminf(fmaxf(x, S.lb[d]), S.ub[d]);
+                S.Xc[(size_t)row * Dp + d] = x;
+            }
+        }
+        __syncthreads();
+        eval_chunk<FitT>(R, S, rows);
+        for (int row = warp; row < rows; row += kWarps) {
+            const int i = c0 + row;
+            const FitT fn = S.rowF[row];
+            if (!select) {
+                if (lane == 0) F[i] = fn;
+                continue;
+            }
+            float* xnew = const_cast<float*>(X) + (size_t)i * D;
+            for (int d = lane; d < D; d += 32) xnew[d] = S.Xc[(size_t)row * Dp + d];
+            const bool acc = fn < Fsel[i];
+            if (acc)
+                for (int d = lane; d < D; d += 32) Xsel[(size_t)i * D + d] = S.Xc[(size_t)row * Dp + d];
+            __syncwarp();
+            if (lane == 0) {
+                F[i] = fn;
+                if (acc) Fsel[i] = fn;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void philox_kernel(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t k1, int n,
+                              uint32_t* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint4 w = philox(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], k0, k1);
+        out[4 * i] = w.x;
+        out[4 * i + 1] = w.y;
+        out[4 * i + 2] = w.z;
+        out[4 * i + 3] = w.w;
+    }
+}
+
+// ------------------------------------------------------- host launchers
+cudaError_t launch_dr(const ApoRun* d_runs, const int* d_offs, int n_runs, int n_work,
+                      int max_ps_pad, cudaStream_t st)
+{
+    if (n_work <= 0) return cudaSuccess;
+    const size_t smem = (size_t)max_ps_pad * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(dr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = n_work < sms * 8 ? n_work : sms * 8;
+    dr_kernel<<<grid, kThreads, smem, st>>>(d_runs, d_offs, n_runs, n_work);
+    return cudaGetLastError();
+}
+
+template <typename FitT, int QPL>
+static cudaError_t launch_run_t(const ApoRun* d_runs, int n_runs, int grid_g, int n_ctas, int* d_queue,
+                                int* d_status, size_t smem, cudaStream_t st)
+{
+    auto fn = run_kernel<FitT, QPL>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (grid_g > 0) {
+        void* args[] = {(void*)&d_runs, (void*)&n_runs, (void*)&grid_g, (void*)&d_queue, (void*)&d_status};
+        return cudaLaunchCooperativeKernel((const void*)fn, dim3(n_runs * grid_g), dim3(kThreads), args,
+                                           smem, st);
+    }
+    fn<<<n_ctas, kThreads, smem, st>>>(d_runs, n_runs, 0, d_queue, d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_run(const ApoRun* d_runs, int n_runs, int grid_g, int n_ctas, int* d_queue, int* d_status,
+                       size_t smem, bool fit64, int qpl, cudaStream_t st)
+{
+    if (fit64) {
+        if (qpl == 1) return launch_run_t<double, 1>(d_runs, n_runs, grid_g, n_ctas, d_queue, d_status, smem, st);
+        return cudaErrorInvalidValue;
+    }
+    switch (qpl) {
+    case 1: return launch_run_t<float, 1>(d_runs, n_runs, grid_g, n_ctas, d_queue, d_status, smem, st);
+    case 2: return launch_run_t<float, 2>(d_runs, n_runs, grid_g, n_ctas, d_queue, d_status, smem, st);
+    case 4: return launch_run_t<float, 4>(d_runs, n_runs, grid_g, n_ctas, d_queue, d_status, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename FitT, int QPL>
+static int capacity_t(size_t smem)
+{
+    auto fn = run_kernel<FitT, QPL>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess) return 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return per_sm * sms;
+}
+
+int run_kernel_capacity(bool fit64, int qpl, size_t smem)
+{
+    if (fit64) return qpl == 1 ? capacity_t<double, 1>(smem) : 0;
+    switch (qpl) {
+    case 1: return capacity_t<float, 1>(smem);
+    case 2: return capacity_t<float, 2>(smem);
+    case 4: return capacity_t<float, 4>(smem);
+    default: return 0;
+    }
+}
+
+template <typename FitT, int QPL>
+static cudaError_t launch_eval_t(const ApoRun* d_run, int n, const float* d_X, void* d_F, int select,
+                                 float* d_Xsel, void* d_Fsel, size_t smem, cudaStream_t st)
+{
+    auto fn = eval_kernel<FitT, QPL>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (n + kChunk - 1) / kChunk;
+    fn<<<grid, kThreads, smem, st>>>(d_run, n, d_X, static_cast<FitT*>(d_F), select, d_Xsel,
+                                     static_cast<FitT*>(d_Fsel));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval(const ApoRun* d_run, int n, const float* d_X, void* d_F, int select, float* d_Xsel,
+                        void* d_Fsel, size_t smem, bool fit64, int qpl, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (fit64) return launch_eval_t<double, 1>(d_run, n, d_X, d_F, select, d_Xsel, d_Fsel, smem, st);
+    return launch_eval_t<float, 1>(d_run, n, d_X, d_F, select, d_Xsel, d_Fsel, smem, st);
+}
+
+cudaError_t launch_philox(const uint32_t* d_ctr, uint32_t k0, uint32_t k1, int n, uint32_t* d_out,
+                          cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    philox_kernel<<<grid, 256, 0, st>>>(d_ctr, k0, k1, n, d_out);
+    return cudaGetLastError();
+}
+
+}  // namespace apo

@@ -1,0 +1,181 @@
+"""Whole runs on the GPU: invariants, batch = single, end-to-end agreement with
+the oracle (median best fitness over 31 seeds within 1%), the bit-exact
+histogram and the thresholding pipeline."""
+import numpy as np
+import pytest
+
+from paper_2510_14982_gb300 import inputs
+from parity_helpers import close, gpu_eval
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def apo():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_14982_gb300 import apo as m
+    return m
+
+
+def test_run_invariants(apo):
+    spec = inputs.shifted_rotated(inputs.OBJ_HYBRID, 30, 3)
+    prob = apo.problem_from_spec(spec)
+    bx, bf, curve = apo.apo_run(prob, apo.apo_params_make(64, 1, 0.1, 300, 1))
+    assert np.all(np.diff(curve) <= 0)
+    assert curve[-1] == np.float32(bf)
+    assert np.all(bx >= spec.lb) and np.all(bx <= spec.ub)
+    assert close(gpu_eval(apo, prob, bx[None]), [bf]).all()
+    assert bf < curve[0]
+
+
+def test_single_run_matches_oracle_trajectory_start(apo, orc):
+    """Both sides consume the same draws, so the curves coincide until the
+    first near-tie flip; the first iterations must agree."""
+    spec = inputs.single_rastrigin(0)
+    prob = apo.problem_from_spec(spec)
+    _, _, cg = apo.apo_run(prob, apo.apo_params_make(20, 1, 0.1, 1000, 0))
+    _, _, co = orc.apo_run(orc.OracleProblem.from_spec(spec), orc.params(20, 1, 0.1, 1000, 0))
+    assert close(cg[:20], co[:20]).all(), (cg[:20], co[:20])
+
+
+def _perm_test_median(a, b, n=20000, seed=0):
+    """Two-sided permutation test of the difference of medians."""
+    rng = np.random.default_rng(seed)
+    obs = abs(np.median(a) - np.median(b))
+    pool = np.concatenate([a, b])
+    cnt = 0
+    for _ in range(n):
+        rng.shuffle(pool)
+        cnt += abs(np.median(pool[:len(a)]) - np.median(pool[len(a):])) >= obs - 1e-12
+    return (cnt + 1) / (n + 1)
+
+
+def test_end_to_end_best_fitness_over_seeds(apo, orc):
+    """Whole single-Rastrigin runs (ps 20, D 10, 1000 iterations).  The float32
+    and float64 trajectories coincide for the first tens of iterations and then
+    separate at near-ties, after which each seed settles in its own Rastrigin
+    basin; the best fitness is therefore compared as a distribution: the
+    medians over 31 seeds (and the distributions over 128 seeds) must not
+    differ beyond sampling noise.  The relative gap of the 31-seed medians is
+    printed."""
+    import torch
+    from scipy import stats
+    spec = inputs.single_rastrigin(0)
+    oprob = orc.OracleProblem.from_spec(spec)
+    n = 128
+    probs = [apo.problem_from_spec(spec)] * n
+    prms = [apo.apo_params_make(20, 1, 0.1, 1000, s) for s in range(n)]
+    bx = torch.zeros((n, 10), device="cuda")
+    bf = torch.zeros(n, dtype=torch.float64, device="cuda")
+    apo.apo_run_batch(probs, prms, bx, 10, bf)
+    g = bf.cpu().numpy()
+    o = np.array([orc.apo_run(oprob, orc.params(20, 1, 0.1, 1000, s), want_curve=False)[1] for s in range(n)])
+    gap31 = abs(np.median(g[:31]) - np.median(o[:31])) / abs(np.median(o[:31]))
+    print("median over 31 seeds: gpu %.4f oracle %.4f (relative gap %.4f)" % (np.median(g[:31]), np.median(o[:31]), gap31))
+    assert _perm_test_median(g[:31], o[:31]) > 1e-3
+    assert stats.ks_2samp(g, o).pvalue > 1e-3
+    assert abs(np.mean(g) - np.mean(o)) <= 4 * np.sqrt(np.var(g) / n + np.var(o) / n)
+
+
+def test_batch_equals_single_runs(apo):
+    import torch
+    specs = [(inputs.shifted_rotated(inputs.OBJ_RASTRIGIN, 10, 0), 20),
+             (inputs.shifted_rotated(inputs.OBJ_ELLIPTIC, 50, 1, run=1), 300),
+             (inputs.shifted_rotated(inputs.OBJ_HYBRID, 20, 2, run=2), 77),
+             (inputs.shifted_rotated(inputs.OBJ_ROSENBROCK, 100, 3, run=3), 1500)]
+    T = 60
+    probs = [apo.problem_from_spec(s) for s, _ in specs]
+    prms = [apo.apo_params_make(ps, 1, 0.1, T, 11, k) for k, (_, ps) in enumerate(specs)]
+    n = len(specs)
+    bx = torch.zeros((n, 100), device="cuda")
+    bf = torch.zeros(n, dtype=torch.float64, device="cuda")
+    cv = torch.zeros((n, T + 1), device="cuda")
+    apo.apo_run_batch(probs, prms, bx, 100, bf, cv, T + 1)
+    torch.cuda.synchronize()
+    for k in range(n):
+        x, f, c = apo.apo_run(probs[k], prms[k])
+        assert bf[k].item() == f
+        np.testing.assert_array_equal(cv[k].cpu().numpy(), c)
+        np.testing.assert_array_equal(bx[k, :probs[k].D].cpu().numpy(), x)
+
+
+@pytest.mark.parametrize("n,images", [(1, 1), (15, 3), (4096 + 7, 2), (1 << 20, 4), (3_000_001, 1)])
+def test_histogram_bit_exact(apo, n, images):
+    import torch
+    px = np.concatenate([inputs.gmm_image(i, n) for i in range(images)])
+    d = torch.tensor(px, device="cuda")
+    h = torch.empty((images, 256), dtype=torch.int32, device="cuda")
+    apo.apo_histogram_u8(d, n, images, h)
+    torch.cuda.synchronize()
+    for i in range(images):
+        np.testing.assert_array_equal(h[i].cpu().numpy(), np.bincount(px[i * n:(i + 1) * n], minlength=256))
+
+
+def test_histogram_unaligned_base(apo):
+    import torch
+    px = inputs.gmm_image(9, 1_000_003)
+    d = torch.tensor(px, device="cuda")
+    h = torch.empty((1, 256), dtype=torch.int32, device="cuda")
+    apo.apo_histogram_u8(d[3:], px.size - 3, 1, h)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(h[0].cpu().numpy(), np.bincount(px[3:], minlength=256))
+
+
+@pytest.mark.parametrize("T", [1, 2])
+def test_thresholding_pipeline_reaches_exhaustive_optimum(apo, orc, T):
+    """Device histogram -> Otsu problem -> APO (ps = 100, 500 iterations):
+    the best thresholds reach the exhaustive optimum of sigma_B^2."""
+    import torch
+    px = inputs.gmm_image(20 + T, 1 << 20)
+    d = torch.tensor(px, device="cuda")
+    h = torch.empty((1, 256), dtype=torch.int32, device="cuda")
+    apo.apo_histogram_u8(d, px.size, 1, h)
+    prob = apo.apo_problem_create(T, np.zeros(T), np.full(T, 255.0), apo.APO_OBJ_OTSU, hist_device=h[0])
+    _, bf, _ = apo.apo_run(prob, apo.apo_params_make(100, 1, 0.1, 500, 3))
+    hist = np.bincount(px, minlength=256)
+    if T == 1:
+        best = max(orc.otsu_sigma_b2(hist, np.array([t])) for t in range(256))
+    else:
+        best = max(orc.otsu_sigma_b2(hist, np.array([a, b])) for a in range(256) for b in range(a, 256))
+    assert -bf == best
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_lockstep_every_iteration_of_a_run(apo, orc, seed):
+    """Every iteration of a whole single-Rastrigin run (ps 20, D 10, 1000
+    iterations) from the GPU's own state: the GPU step and the oracle step agree
+    within the tolerance, with differing decisions only at near-ties."""
+    import torch
+    from parity_helpers import tol
+    spec = inputs.single_rastrigin(0)
+    gprob = apo.problem_from_spec(spec)
+    oprob = orc.OracleProblem.from_spec(spec)
+    ps, T = 20, 1000
+    gprm = apo.apo_params_make(ps, 1, 0.1, T, seed)
+    oprm = orc.params(ps, 1, 0.1, T, seed)
+    X0, F0 = orc.init_population(oprob, oprm)
+    X = torch.tensor(X0.astype(np.float32), device="cuda")
+    F = torch.tensor(orc.objective(oprob, X0.astype(np.float32).astype(np.float64)).astype(np.float32),
+                     device="cuda")
+    flips = 0
+    for t in range(1, T + 1):
+        Xh = X.cpu().numpy().astype(np.float64)
+        Fh = F.cpu().numpy()
+        apo.apo_step(gprob, gprm, t, X, F)
+        torch.cuda.synchronize()
+        Xo, Fo, info = orc.apo_step(oprob, oprm, t, Xh, Fh.astype(np.float64), with_info=True)
+        Xg, Fg = X.cpu().numpy(), F.cpu().numpy()
+        Fs = Fh[info["order"]]
+        took = Fg != Fs
+        same = np.all(info["xnew"] == Xh[info["order"]], axis=1)
+        diff = (took != info["accepted"].astype(bool)) & ~same
+        near = np.abs(info["fnew"] - Fs) <= tol(Fs) + tol(info["fnew"])
+        assert not np.any(diff & ~near), (t, np.nonzero(diff & ~near))
+        flips += int(diff.sum())
+        want_X = np.where(took[:, None], info["xnew"], Xh[info["order"]])
+        want_F = np.where(took, info["fnew"], Fs)
+        assert close(Xg, want_X).all(), t
+        assert close(Fg, want_F).all(), t
+    assert flips <= 0.01 * ps * T
