@@ -1,0 +1,299 @@
+"""Benchmark of the APO population update on GB300.
+
+Default workload ("scale"): plain APO at population 4096, D = 100, 2000
+iterations, on the four seeded shifted-rotated forms (ill-conditioned
+elliptic, chained Rosenbrock, Rastrigin cosine sum, 30/30/40 hybrid).  One
+step = one complete run of each of the four forms (4 x 4096 x 2000 candidate
+updates, each evaluated exactly once, plus 4 x 4096 initial evaluations),
+issued as one apo_run_batch call.  Metric: candidate updates/s (whole job,
+all GPUs); true evaluations/s is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+                  [--iters T] [--workload scale|single]
+
+Multi-GPU: the runs are independent, so N ranks run N replicas (weak
+scaling); torch.distributed only carries the timing barrier and the max over
+ranks.  --impl reference times the FP64 CPU oracle (the only reference the
+paper's method has here) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2510_14982_gb300 import inputs  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SMS = 152                 # GB300 streaming multiprocessors
+FP32_LANES = 128          # FP32 FMA lanes per SM
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        p["source"] = "measured"
+        return p
+    except OSError:
+        p = dict(FALLBACK)
+        p["source"] = "fallback"
+        return p
+
+
+def workload(name, iters):
+    """(specs, ps, T, label) of a named workload."""
+    if name == "scale":
+        return inputs.scale_forms(seed=0, D=100), 4096, iters or 2000, "plain APO ps=4096 D=100 x4 forms"
+    if name == "single":
+        return [inputs.single_rastrigin(0)], 20, iters or 1000, "plain APO ps=20 D=10 Rastrigin"
+    raise SystemExit("unknown workload " + name)
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_sample(specs, ps, T_sample, n_threads):
+    """Times the FP64 oracle, as it stands, on a bounded sample: one run of each
+    form with T_sample iterations, the forms spread over n_threads host threads.
+    Returns (candidate updates/s, seconds, threads used)."""
+    import oracle
+    oracle.build()
+    probs = [oracle.OracleProblem.from_spec(s) for s in specs]
+    prms = [oracle.params(ps, 1, 0.1, T_sample, 1000 + k, k) for k in range(len(specs))]
+    threads = max(1, min(n_threads, len(specs)))
+    t0 = time.perf_counter()
+    oracle.apo_run_many(probs, prms, threads)
+    dt = time.perf_counter() - t0
+    return len(specs) * ps * T_sample / dt, dt, threads
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle on the host cores."""
+    world, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    specs, ps, T, label = workload(args.workload, args.iters)
+    T_sample = args.ref_iters
+    cores = os.cpu_count() or 1
+    times = []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        cpu_oracle_sample(specs, ps, max(1, T_sample // 4), cores)
+    for _ in range(args.steps):
+        v, dt, thr = cpu_oracle_sample(specs, ps, T_sample, cores)
+        times.append(dt)
+    per_step = statistics.mean(times)
+    value = len(specs) * ps * T_sample / per_step
+    sample = "%d forms x ps %d x %d iterations per step (full run: %d iterations), %d threads" % (
+        len(specs), ps, T_sample, T, thr)
+    line = {"impl": "reference", "metric": "APO candidate updates/s", "value": value, "unit": "updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": label, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": thr, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def flush_l2(buf):
+    buf.add_(1)   # writes 256 MiB, larger than the 129 MB L2
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "single"])
+    ap.add_argument("--iters", type=int, default=0, help="override the iteration count (profiling)")
+    ap.add_argument("--ref-iters", type=int, default=40, help="oracle iterations per timed sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2510_14982_gb300 import apo
+
+    specs, ps, T, label = workload(args.workload, args.iters)
+    n = len(specs)
+    Dmax = max(s.D for s in specs)
+    probs = [apo.problem_from_spec(s) for s in specs]
+    dev = torch.device("cuda", local)
+    bx = torch.zeros((n, Dmax), device=dev)
+    bf = torch.zeros(n, dtype=torch.float64, device=dev)
+    cv = torch.zeros((n, T + 1), device=dev)
+    flush = torch.zeros(64 << 20, dtype=torch.float32, device=dev)
+    ev_run0 = torch.cuda.Event(enable_timing=True)
+    ev_run1 = torch.cuda.Event(enable_timing=True)
+    ev_run0.record()   # torch creates the cudaEvent_t on first record
+    ev_run1.record()
+
+    def step(k):
+        prms = [apo.apo_params_make(ps, 1, 0.1, T, 100 * k + rank, j) for j in range(n)]
+        apo.apo_run_batch(probs, prms, bx, Dmax, bf, cv, T + 1)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    apo.apo_set_timing_events(ev_run0, ev_run1)
+    step_ms, run_ms = [], []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            e0.record()
+            step(args.warmup + k)
+            e1.record()
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            run_ms.append(ev_run0.elapsed_time(ev_run1))
+    apo.apo_set_timing_events(None, None)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        total_ms = float(t.item())
+    updates = world * args.steps * n * ps * T
+    evals = world * args.steps * n * ps * (T + 1)
+    value = updates / (total_ms * 1e-3)
+
+    # end to end through the public API: problem upload from host memory,
+    # the batch call, and the results read back into pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host_bx = torch.empty((n, Dmax), pin_memory=True)
+        host_bf = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        host_cv = torch.empty((n, T + 1), pin_memory=True)
+        h2d = sum(4 * (s.D * s.D + s.D) + 16 * s.D + (0 if s.perm is None else 4 * s.D) for s in specs)
+        d2h = host_bx.numel() * 4 + host_bf.numel() * 8 + host_cv.numel() * 4
+        e2e_s = []
+        for k in range(args.steps):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ps_k = [apo.problem_from_spec(s) for s in specs]
+            prms = [apo.apo_params_make(ps, 1, 0.1, T, 7000 + 100 * k + rank, j) for j in range(n)]
+            apo.apo_run_batch(ps_k, prms, bx, Dmax, bf, cv, T + 1)
+            host_bx.copy_(bx, non_blocking=True)
+            host_bf.copy_(bf, non_blocking=True)
+            host_cv.copy_(cv, non_blocking=True)
+            torch.cuda.synchronize()
+            del ps_k
+            e2e_s.append(time.perf_counter() - t0)
+        e2e_v = n * ps * T * args.steps / sum(e2e_s) * world
+        e2e = {"value": e2e_v, "unit": "updates/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    pk = peaks()
+    clocks = clk.summary()
+    # dominant kernel: the iteration-loop kernel; algorithmic work per launch is
+    # the rotation z = M (x - o) of every evaluation, 2 D^2 flop each
+    flop_per_launch = sum(2.0 * s.D * s.D * ps * (T + 1) for s in specs)
+    run_avg_s = statistics.mean(run_ms) * 1e-3
+    achieved = flop_per_launch / run_avg_s / 1e12
+    fp32_peak = SMS * FP32_LANES * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    line = {
+        "metric": "APO candidate updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": label, "runs_per_step": n, "ps": ps, "D": Dmax, "iterations": T,
+                   "np": 1, "pf_max": 0.1, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "true_evals_per_s": evals / (total_ms * 1e-3),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "kernel": "run_kernel (FP32 FMA rotation, 2 D^2 flop per evaluation)",
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s clock)" % (
+                         float(pk.get("sm_max_mhz", 2070.0)), pk["source"]),
+                     "kernel_ms": statistics.mean(run_ms)},
+        "clocks": clocks,
+        "gpu_launches": 2 * args.steps,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, thr = cpu_oracle_sample(specs, ps, args.ref_iters, os.cpu_count() or 1)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": thr, "kind": "oracle",
+                                "sample": "%d forms x ps %d x %d iterations (%.1f s)" % (n, ps, args.ref_iters, dt)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -164,6 +164,14 @@ apo_status apo_histogram_u8(const uint8_t* d_pixels, int64_t n_pixels_per_image,
 apo_status apo_philox4x32_10(const uint32_t* d_ctr, uint32_t key0, uint32_t key1, int n,
                              uint32_t* d_out, void* stream);
 
+/* Instrumentation: when set (non-NULL cudaEvent_t handles), every later
+ * apo_run / apo_run_device / apo_run_batch call records `before` on its
+ * stream immediately before its first iteration-loop kernel and `after`
+ * immediately after its last, so that a caller can time those kernels with
+ * cudaEventElapsedTime.  Process-wide setting; pass NULL, NULL to clear.  The
+ * caller keeps ownership of the events. */
+apo_status apo_set_timing_events(void* before, void* after);
+
 const char* apo_status_string(apo_status status);
 const char* apo_last_error(void);
 

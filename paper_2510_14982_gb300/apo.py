@@ -28,7 +28,7 @@ APO_OK, APO_ERR_INVALID_ARG, APO_ERR_CUDA, APO_ERR_OOM, APO_ERR_TIMEOUT, APO_ERR
 # every entry point declared in include/apo.h
 EXPORTS = ("apo_problem_create", "apo_problem_destroy", "apo_problem_dim", "apo_run", "apo_run_device",
            "apo_run_batch", "apo_step", "apo_evaluate", "apo_clamp_eval_select", "apo_histogram_u8",
-           "apo_philox4x32_10", "apo_status_string", "apo_last_error")
+           "apo_philox4x32_10", "apo_set_timing_events", "apo_status_string", "apo_last_error")
 
 
 class apo_objective_desc(C.Structure):
@@ -60,6 +60,8 @@ _lib.apo_evaluate.argtypes = [_P, _P, _P, C.c_int, _P]
 _lib.apo_clamp_eval_select.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
 _lib.apo_histogram_u8.argtypes = [_P, C.c_int64, C.c_int, _P, _P]
 _lib.apo_philox4x32_10.argtypes = [_P, C.c_uint32, C.c_uint32, C.c_int, _P, _P]
+_lib.apo_set_timing_events.argtypes = [_P, _P]
+_lib.apo_set_timing_events.restype = C.c_int
 for _f in ("apo_run", "apo_run_device", "apo_run_batch", "apo_step", "apo_evaluate", "apo_clamp_eval_select",
            "apo_histogram_u8", "apo_philox4x32_10"):
     getattr(_lib, _f).restype = C.c_int
@@ -219,6 +221,15 @@ def apo_histogram_u8(d_pixels, n_per_image, n_images, d_hist, stream=None):
 def apo_philox4x32_10(d_ctr, key0, key1, d_out, stream=None):
     _check(_lib.apo_philox4x32_10(_dptr(d_ctr), int(key0) & 0xFFFFFFFF, int(key1) & 0xFFFFFFFF,
                                   int(d_ctr.numel() // 4), _dptr(d_out), _stream(stream)), "apo_philox4x32_10")
+
+
+def apo_set_timing_events(before, after):
+    """before / after: torch.cuda.Event objects (or None, None to clear)."""
+    if before is not None and (not before.cuda_event or not after.cuda_event):
+        raise ValueError("record the events once before registering them (torch creates them lazily)")
+    b = None if before is None else C.c_void_p(before.cuda_event)
+    a = None if after is None else C.c_void_p(after.cuda_event)
+    _check(_lib.apo_set_timing_events(b, a), "apo_set_timing_events")
 
 
 def raw_lib():

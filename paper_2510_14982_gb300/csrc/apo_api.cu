@@ -54,6 +54,9 @@ constexpr int kQueueMaxPs = 1024;
 // Minimum protozoa per CTA in grid mode.
 constexpr int kGridMinRows = 8;
 
+// Optional timing events around the iteration-loop kernels.
+cudaEvent_t g_ev_before = nullptr, g_ev_after = nullptr;
+
 }  // namespace
 
 struct apo_problem {
@@ -650,11 +653,14 @@ apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
     }
     ApoRun* d_ordered = nullptr;
     APO_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_ordered), sizeof(ApoRun) * ordered.size(), st));
+    if (nl > 64) { set_err("too many launch groups"); return fail(APO_ERR_INTERNAL); }
     e = cudaMemcpyAsync(d_ordered, ordered.data(), sizeof(ApoRun) * ordered.size(), cudaMemcpyHostToDevice, st);
+    const bool timed = g_ev_before && g_ev_after && !(specs[0].flags & kFlagStepOut);
+    if (timed && e == cudaSuccess) e = cudaEventRecord(g_ev_before, st);
     for (size_t l = 0; l < nl && e == cudaSuccess; ++l) {
         Group& gr = *launches[l].first;
         const int cnt = (int)launches[l].second.size();
-        int* queue = reinterpret_cast<int*>(base + off_ctrl) + (int)l % 64;
+        int* queue = reinterpret_cast<int*>(base + off_ctrl) + (int)l;
         if (gr.grid) {
             e = launch_run(d_ordered + first[l], cnt, ordered[first[l]].g, 0, queue, status, gr.smem, gr.fit64,
                            gr.qpl, st);
@@ -665,9 +671,9 @@ apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
                            gr.qpl, st);
         }
     }
+    if (timed && e == cudaSuccess) e = cudaEventRecord(g_ev_after, st);
     cudaFreeAsync(d_ordered, st);
     if (e != cudaSuccess) { set_err("run launch failed: %s", cudaGetErrorString(e)); return fail(APO_ERR_CUDA); }
-    if (nl > 64) { set_err("too many launch groups"); return fail(APO_ERR_INTERNAL); }
     APO_CUDA(cudaFreeAsync(ws, st));
     return APO_OK;
 }
@@ -821,6 +827,14 @@ extern "C" apo_status apo_histogram_u8(const uint8_t* d_pixels, int64_t n_pixels
     const cudaError_t e = launch_histogram_u8(d_pixels, n_pixels_per_image, n_images, d_hist,
                                               static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) { set_err("histogram launch failed: %s", cudaGetErrorString(e)); return APO_ERR_CUDA; }
+    return APO_OK;
+}
+
+extern "C" apo_status apo_set_timing_events(void* before, void* after)
+{
+    if ((before == nullptr) != (after == nullptr)) { set_err("set both events or neither"); return APO_ERR_INVALID_ARG; }
+    g_ev_before = static_cast<cudaEvent_t>(before);
+    g_ev_after = static_cast<cudaEvent_t>(after);
     return APO_OK;
 }
 
