@@ -124,6 +124,25 @@ apo_status apo_run(const apo_problem* prob, const apo_params* params, void* stre
 apo_status apo_run_device(const apo_problem* prob, const apo_params* params, void* stream,
                           float* d_best_x, double* d_best_f, float* d_curve);
 
+/* apo_run_device for callers that cannot allocate device memory: callers
+ * whose device memory is entirely reserved by their own pool or framework,
+ * where a cudaMalloc would fail or take memory the pool accounts for, and
+ * callers in latency-critical loops that cannot accept the device-wide
+ * synchronisation a cudaFree implies.  The paper has no counterpart; this is
+ * a deployment variant of apo_run_device with the same arguments and results.
+ * It calls no cudaMalloc, cudaFree or allocating library routine: its
+ * workspace is one file-scope device array of 8 MiB that every device loading
+ * the library holds until the process exits, looked up on the first call on
+ * each device (make that first call before any stream capture).  A run whose
+ * workspace exceeds 8 MiB (roughly ps * D * 8 bytes when ps > 1024 or the
+ * population does not fit in shared memory, plus (max_iter + 1) * ps / 8
+ * bytes) is rejected with APO_ERR_UNSUPPORTED and a message naming the size.
+ * Every call shares the array and clears what must start at zero; calls that
+ * overlap on the GPU (other host threads or streams) race on it.  Returns
+ * after the run has finished (synchronises `stream`). */
+apo_status apo_run_device_noalloc(const apo_problem* prob, const apo_params* params, void* stream,
+                                  float* d_best_x, double* d_best_f, float* d_curve);
+
 /* n_runs independent runs in as few launches as possible (a persistent
  * work-queue launch for runs whose population fits in shared memory, a
  * cooperative grid launch for the rest).  Run k uses probs[k] and params[k]

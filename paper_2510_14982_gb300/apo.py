@@ -27,6 +27,7 @@ APO_OK, APO_ERR_INVALID_ARG, APO_ERR_CUDA, APO_ERR_OOM, APO_ERR_TIMEOUT, APO_ERR
 
 # every entry point declared in include/apo.h
 EXPORTS = ("apo_problem_create", "apo_problem_destroy", "apo_problem_dim", "apo_run", "apo_run_device",
+           "apo_run_device_noalloc",
            "apo_run_batch", "apo_step", "apo_evaluate", "apo_clamp_eval_select", "apo_histogram_u8",
            "apo_philox4x32_10", "apo_set_timing_events", "apo_status_string", "apo_last_error")
 
@@ -54,6 +55,7 @@ _lib.apo_problem_dim.restype = C.c_int
 _lib.apo_run.argtypes = [_P, C.POINTER(apo_params), _P, C.POINTER(C.c_float), C.POINTER(C.c_double),
                          C.POINTER(C.c_float)]
 _lib.apo_run_device.argtypes = [_P, C.POINTER(apo_params), _P, _P, _P, _P]
+_lib.apo_run_device_noalloc.argtypes = [_P, C.POINTER(apo_params), _P, _P, _P, _P]
 _lib.apo_run_batch.argtypes = [C.POINTER(_P), C.POINTER(apo_params), C.c_int, _P, _P, C.c_int, _P, _P, C.c_int]
 _lib.apo_step.argtypes = [_P, C.POINTER(apo_params), C.c_int, _P, _P, _P]
 _lib.apo_evaluate.argtypes = [_P, _P, _P, C.c_int, _P]
@@ -62,7 +64,7 @@ _lib.apo_histogram_u8.argtypes = [_P, C.c_int64, C.c_int, _P, _P]
 _lib.apo_philox4x32_10.argtypes = [_P, C.c_uint32, C.c_uint32, C.c_int, _P, _P]
 _lib.apo_set_timing_events.argtypes = [_P, _P]
 _lib.apo_set_timing_events.restype = C.c_int
-for _f in ("apo_run", "apo_run_device", "apo_run_batch", "apo_step", "apo_evaluate", "apo_clamp_eval_select",
+for _f in ("apo_run", "apo_run_device", "apo_run_device_noalloc", "apo_run_batch", "apo_step", "apo_evaluate", "apo_clamp_eval_select",
            "apo_histogram_u8", "apo_philox4x32_10"):
     getattr(_lib, _f).restype = C.c_int
 _lib.apo_status_string.argtypes = [C.c_int]
@@ -188,6 +190,12 @@ def apo_run(prob: Problem, params: apo_params, stream=None, want_curve=True):
 def apo_run_device(prob: Problem, params: apo_params, d_best_x, d_best_f, d_curve=None, stream=None):
     _check(_lib.apo_run_device(prob.handle, C.byref(params), _stream(stream), _dptr(d_best_x), _dptr(d_best_f),
                                _dptr(d_curve)), "apo_run_device")
+
+
+def apo_run_device_noalloc(prob: Problem, params: apo_params, d_best_x, d_best_f, d_curve=None, stream=None):
+    """apo_run_device without any device allocation (shared static scratch; synchronous)."""
+    _check(_lib.apo_run_device_noalloc(prob.handle, C.byref(params), _stream(stream), _dptr(d_best_x),
+                                       _dptr(d_best_f), _dptr(d_curve)), "apo_run_device_noalloc")
 
 
 def apo_run_batch(probs, params, d_best_x, x_stride, d_best_f, d_curves=None, curve_stride=0, stream=None):

@@ -59,13 +59,6 @@ cudaEvent_t g_ev_before = nullptr, g_ev_after = nullptr;
 
 }  // namespace
 
-struct apo_problem {
-    int device;
-    int D, Dp, kind, ncomp;
-    int any_rot;
-    DevProblem dev;
-    void* mem;
-};
 
 // ------------------------------------------------------------ errors
 extern "C" const char* apo_status_string(apo_status s)
@@ -83,6 +76,8 @@ extern "C" const char* apo_status_string(apo_status s)
 }
 
 extern "C" const char* apo_last_error(void) { return g_err; }
+
+void apo::set_last_error(const char* msg) { set_err("%s", msg); }
 
 // ---------------------------------------------------------- problems
 namespace {

@@ -7,6 +7,17 @@
 
 #include "apo_device.cuh"
 
+// A problem created by apo_problem_create: device copies of the bounds,
+// shifts, (transposed, permuted) rotations, elliptic weights and Otsu tables
+// in one allocation `mem`, described by `dev`.
+struct apo_problem {
+    int device;
+    int D, Dp, kind, ncomp;
+    int any_rot;
+    apo::DevProblem dev;
+    void* mem;
+};
+
 namespace apo {
 
 // Launches the Dr_index selection (Eq. 11) for every (run, t) of the runs:
@@ -32,6 +43,9 @@ int run_kernel_capacity(bool fit64, int qpl, size_t smem_bytes);
 cudaError_t launch_eval(const ApoRun* d_run, int n, const float* d_X, void* d_F, int select,
                         float* d_Xsel, void* d_Fsel, size_t smem_bytes, bool fit64, int qpl,
                         cudaStream_t st);
+
+// Sets the text that apo_last_error() returns on the calling thread.
+void set_last_error(const char* msg);
 
 cudaError_t launch_philox(const uint32_t* d_ctr, uint32_t k0, uint32_t k1, int n, uint32_t* d_out,
                           cudaStream_t st);
