@@ -15,6 +15,7 @@
 
 #include "../../include/apo.h"
 #include "apo_internal.h"
+#include "apo_plan.h"
 
 using namespace apo;
 
@@ -417,51 +418,6 @@ apo_status check_params(const apo_problem* P, const apo_params* p)
 
 int qpl_of(const apo_problem* P) { return P->D <= 64 ? 1 : (P->D <= 128 ? 2 : 4); }
 
-// Shared-memory layout of one run (kept in step with the device carve()).
-SmemPlan make_plan(const apo_problem* P, int ps, bool resident, bool mt_smem)
-{
-    const bool fit64 = P->kind == APO_OBJ_OTSU;
-    const size_t fsz = fit64 ? 8 : 4;
-    const int Dp = P->Dp;
-    SmemPlan L;
-    std::memset(&L, 0, sizeof(L));
-    L.ps_pad = ps > 0 ? next_pow2(ps) : 0;
-    L.resident = resident;
-    L.mt_smem = mt_smem;
-    size_t off = 0;
-    auto take = [&](size_t bytes) -> uint32_t {
-        off = align_up(off, 16);
-        const uint32_t at = (uint32_t)off;
-        off += bytes;
-        return at;
-    };
-    L.X0 = take(resident ? (size_t)ps * Dp * 4 : 0);
-    L.X1 = take(resident ? (size_t)ps * Dp * 4 : 0);
-    L.F0 = take(resident ? ps * fsz : 0);
-    L.F1 = take(resident ? ps * fsz : 0);
-    L.perm0 = take((size_t)L.ps_pad * 4);
-    L.perm1 = take((size_t)L.ps_pad * 4);
-    L.keys = take((size_t)L.ps_pad * (fit64 ? 16 : 8));
-    L.MT = take(mt_smem ? (size_t)Dp * Dp * 4 : 0);
-    L.o = take(Dp * 4);
-    L.lb = take(Dp * 4);
-    L.ub = take(Dp * 4);
-    L.ew = take(Dp * 4);
-    L.Xc = take((size_t)kChunk * Dp * 4);
-    L.Yc = take((size_t)kChunk * Dp * 4);
-    L.Zc = take(P->any_rot ? (size_t)kChunk * Dp * 4 : 0);
-    L.rowF = take(kChunk * fsz);
-    L.compG = take(P->ncomp > 1 ? (size_t)kChunk * kMaxComp * 4 : 0);
-    L.compA = take(P->ncomp > 1 ? (size_t)kChunk * kMaxComp * 4 : 0);
-    L.P0 = take(fit64 ? 256 * 8 : 0);
-    L.P1 = take(fit64 ? 256 * 8 : 0);
-    L.otsu = take(fit64 ? kWarps * 32 * 4 : 0);
-    L.red = take((size_t)kThreads * 16);
-    L.total = (uint32_t)align_up(off, 16);
-    return L;
-}
-
-bool mt_fits(const apo_problem* P) { return P->ncomp == 1 && P->dev.comp[0].MT && (size_t)P->Dp * P->Dp * 4 <= 72 * 1024; }
 
 // One run of a launch plan.
 struct RunSpec {
@@ -500,12 +456,13 @@ apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
     for (int k = 0; k < n; ++k) {
         const RunSpec& s = specs[k];
         const int ps = s.prm.ps;
-        const bool mts = mt_fits(s.P);
-        const SmemPlan res = make_plan(s.P, ps, true, mts);
-        const SmemPlan nres = make_plan(s.P, ps, false, mts);
+        const SmemPlan res = choose_plan(s.P, ps, true, false, kSmemMax);
+        const SmemPlan nres = choose_plan(s.P, ps, false, false, kSmemMax);
         if (ps > kQueueMaxPs) {
             grid[k] = 1;
-            plans[k] = nres;
+            const SmemPlan gp = choose_plan(s.P, ps, false, true, kSmemMax);
+            plans[k] = gp;
+            if (gp.total > kSmemMax) { set_err("population %d needs too much shared memory", ps); return APO_ERR_UNSUPPORTED; }
             if (nres.total > kSmemMax) { set_err("population %d needs too much shared memory", ps); return APO_ERR_UNSUPPORTED; }
         } else if (res.total <= kSmemMax) {
             plans[k] = res;
@@ -536,7 +493,7 @@ apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
     const size_t off_runs = take(sizeof(ApoRun) * n);
     const size_t off_offs = take(sizeof(int) * (n + 1));
     const size_t off_ctrl = take(sizeof(int) * 64);
-    std::vector<size_t> off_dr(n), off_x0(n), off_x1(n), off_f0(n), off_f1(n), off_bar(n);
+    std::vector<size_t> off_dr(n), off_x0(n), off_x1(n), off_f0(n), off_f1(n), off_bar(n), off_pg(n), off_kg(n);
     int n_work = 0;
     std::vector<int> offs(n + 1, 0);
     int max_ps_pad = 1;
@@ -547,6 +504,8 @@ apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
         const int W = (ps + 31) / 32;
         off_dr[k] = take(sizeof(uint32_t) * W * (size_t)(s.t_end + 1));
         const bool need_global = !plans[k].resident || (s.flags & kFlagStepOut);
+        off_pg[k] = grid[k] ? take((size_t)ps * 4) : 0;
+        off_kg[k] = grid[k] ? take((size_t)ps * (s.P->kind == APO_OBJ_OTSU ? 16 : 8)) : 0;
         off_x0[k] = need_global ? take((size_t)ps * Dp * 4) : 0;
         off_x1[k] = need_global ? take((size_t)ps * Dp * 4) : 0;
         off_f0[k] = need_global ? take(ps * fsz) : 0;
@@ -593,6 +552,10 @@ apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
         R.F_out = s.F_in;
         R.best_x = s.best_x; R.best_f = s.best_f; R.curve = s.curve;
         R.bar = reinterpret_cast<unsigned*>(base + off_bar[k]);
+        if (grid[k]) {
+            R.perm_g = reinterpret_cast<uint32_t*>(base + off_pg[k]);
+            R.keys_g = base + off_kg[k];
+        }
     }
     // grid group sizes: g CTAs per run, all co-resident
     std::vector<std::pair<Group*, std::vector<int>>> launches;  // (group, run subset)
@@ -602,7 +565,7 @@ apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
             launches.emplace_back(&gr, gr.runs);
             continue;
         }
-        const int cap = run_kernel_capacity(gr.fit64, gr.qpl, gr.smem);
+        const int cap = run_kernel_capacity(gr.fit64, gr.qpl, gr.smem, true);
         if (cap <= 0) { set_err("grid kernel cannot be resident with %zu B of shared memory", gr.smem); return fail(APO_ERR_UNSUPPORTED); }
         // split into launches of at most `cap` runs (one CTA each at least)
         for (size_t i = 0; i < gr.runs.size(); i += (size_t)cap) {
@@ -660,7 +623,7 @@ apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
             e = launch_run(d_ordered + first[l], cnt, ordered[first[l]].g, 0, queue, status, gr.smem, gr.fit64,
                            gr.qpl, st);
         } else {
-            const int cap = run_kernel_capacity(gr.fit64, gr.qpl, gr.smem);
+            const int cap = run_kernel_capacity(gr.fit64, gr.qpl, gr.smem, false);
             if (cap <= 0) { e = cudaErrorInvalidConfiguration; break; }
             e = launch_run(d_ordered + first[l], cnt, 0, std::min(cap, cnt), queue, status, gr.smem, gr.fit64,
                            gr.qpl, st);
@@ -782,7 +745,7 @@ apo_status eval_common(const apo_problem* P, void* stream, int n, const float* d
     ApoRun R;
     std::memset(&R, 0, sizeof(R));
     R.prob = P->dev;
-    R.plan = make_plan(P, 0, false, mt_fits(P));
+    R.plan = choose_plan(P, 0, false, false, kSmemMax);
     R.g = 1;
     void* d = nullptr;
     APO_CUDA(cudaMallocAsync(&d, sizeof(ApoRun), st));

@@ -10,9 +10,12 @@
 
 namespace apo {
 
-constexpr int kThreads = 256;     // threads per CTA of every APO kernel
+constexpr int kThreads = 256;     // threads per CTA of the work-queue (resident) kernels
 constexpr int kWarps = kThreads / 32;
-constexpr int kChunk = 32;        // candidate rows evaluated together
+constexpr int kGridThreads = 512; // threads per CTA of the cooperative grid kernel
+constexpr int kMaxWarps = kGridThreads / 32;
+constexpr int kChunk = 32;        // candidate rows evaluated together (resident mode)
+constexpr int kGridChunk = 64;    // candidate rows evaluated together (grid mode)
 constexpr int kMaxComp = 10;      // composition components
 
 // Counter slots of the Philox stream: counter = (iter, p, d, slot).
@@ -58,7 +61,9 @@ struct SmemPlan {
     int ps_pad;          // power of two >= ps
     int resident;        // population lives in shared memory
     int mt_smem;         // rotation of component 0 lives in shared memory
-    uint32_t X0, X1, F0, F1, perm0, perm1, keys, MT, o, lb, ub, ew, Xc, Yc, Zc,
+    int chunk;           // candidate rows evaluated together
+    int threads;         // CTA size the plan was made for
+    uint32_t X0, X1, F0, F1, perm0, perm1, keys, MT, o, lb, ub, ew, Xc, Xo, Yc, Zc,
         rowF, compG, compA, P0, P1, otsu, red, total;
 };
 
@@ -84,6 +89,8 @@ struct ApoRun {
     double* best_f;          // [1]
     float* curve;            // [T+1] or nullptr
     unsigned* bar;           // grid barrier words {count, generation, abort}
+    uint32_t* perm_g;        // grid mode: [ps] rank -> slot of the current iteration
+    void* keys_g;            // grid mode: [ps] key segments, each CTA's sorted
 };
 
 // ---------------------------------------------------------------- Philox

@@ -27,16 +27,18 @@ cudaError_t launch_dr(const ApoRun* d_runs, const int* d_offs, int n_runs, int n
                       int max_ps_pad, cudaStream_t st);
 
 // Launches the APO iteration loop.  grid_g > 0: cooperative launch of
-// n_runs * grid_g CTAs, CTA b serving run b / grid_g.  grid_g == 0: a
-// persistent work-queue launch of n_ctas CTAs popping runs from *d_queue.
+// n_runs * grid_g CTAs of the grid kernel (512 threads), CTA b serving run
+// b / grid_g.  grid_g == 0: a persistent work-queue launch of n_ctas CTAs
+// (256 threads) popping runs from *d_queue.
 // fit64 selects float64 fitness (Otsu); qpl is the dimension-pair count per
 // lane (1, 2 or 4).
 cudaError_t launch_run(const ApoRun* d_runs, int n_runs, int grid_g, int n_ctas, int* d_queue,
                        int* d_status, size_t smem_bytes, bool fit64, int qpl, cudaStream_t st);
 
-// Largest number of co-resident CTAs of the run kernel for this shared-memory
-// size (0 on error).
-int run_kernel_capacity(bool fit64, int qpl, size_t smem_bytes);
+// Largest number of co-resident CTAs of the work-queue kernel (grid = false)
+// or of the cooperative grid kernel (grid = true) for this shared-memory size
+// (0 on error).
+int run_kernel_capacity(bool fit64, int qpl, size_t smem_bytes, bool grid);
 
 // Evaluation hooks: rows of d_X [n][D]; select != 0 applies Sec. 4.1 step 6
 // (clamp d_Xnew in place, evaluate into d_Fnew, greedy into d_X / d_F).

@@ -140,7 +140,7 @@ struct Smem {
     void* keys;
     float* MT;
     float *o, *lb, *ub, *ew;
-    float *Xc, *Yc, *Zc;
+    float *Xc, *Xo, *Yc, *Zc;
     FitT* rowF;
     float *compG, *compA;
     long long *P0, *P1;
@@ -165,6 +165,7 @@ __device__ __forceinline__ Smem<FitT> carve(unsigned char* base, const SmemPlan&
     S.ub = reinterpret_cast<float*>(base + L.ub);
     S.ew = reinterpret_cast<float*>(base + L.ew);
     S.Xc = reinterpret_cast<float*>(base + L.Xc);
+    S.Xo = reinterpret_cast<float*>(base + L.Xo);
     S.Yc = reinterpret_cast<float*>(base + L.Yc);
     S.Zc = reinterpret_cast<float*>(base + L.Zc);
     S.rowF = reinterpret_cast<FitT*>(base + L.rowF);
@@ -326,9 +327,9 @@ __device__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S, int rows)
 {
     const DevProblem& P = R.prob;
     const int D = P.D, Dp = P.Dp;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (P.kind == kOtsu) {
-        for (int row = warp; row < rows; row += kWarps) {
+        for (int row = warp; row < rows; row += nw) {
             const double f = otsu_row(S.Xc + (size_t)row * Dp, D, S.P0, S.P1, S.otsu + warp * 32);
             if (lane == 0) S.rowF[row] = (FitT)f;
         }
@@ -351,7 +352,7 @@ __device__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S, int rows)
             __syncthreads();
         }
         const float* ew = (c == 0) ? S.ew : C.ew;
-        for (int row = warp; row < rows; row += kWarps) {
+        for (int row = warp; row < rows; row += nw) {
             const float v = seg_value(Z + (size_t)row * Dp, C, ew, D);
             if (P.ncomp == 1) {
                 if (lane == 0) S.rowF[row] = (FitT)v;
@@ -372,7 +373,7 @@ __device__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S, int rows)
     }
     if (P.ncomp > 1) {
         // f = sum_k w_k (g_k + bias_k) / sum_k w_k, w_k = exp(a_k - max a).
-        for (int row = warp; row < rows; row += kWarps) {
+        for (int row = warp; row < rows; row += nw) {
             const bool on = lane < P.ncomp;
             const float a = on ? S.compA[row * kMaxComp + lane] : -INFINITY;
             const float amax = warp_max(a);
@@ -420,24 +421,73 @@ __device__ void gen_init_row(const ApoRun& R, const Smem<FitT>& S, int p, int ro
 // One candidate (rank r, 0-based) by one warp: mode selection (Eq. 12-13,
 // Algorithm 1), masks (Eq. 3, Eq. 5), dormancy (Eq. 1), reproduction
 // (Eq. 2), autotrophic (Eq. 6-7) or heterotrophic (Eq. 8-10) foraging, then
-// the bound clamp.  Writes row `row` of Xc.
+// the bound clamp.  Writes row `row` of Xc (candidate) and of Xo (the old
+// position, kept for the greedy replacement).  The per-protozoon draws are
+// computed once per warp, one Philox call per lane; the gathered rows are
+// requested before the per-dimension draws and the mask selection so that
+// their latency overlaps that arithmetic.
 template <typename FitT, int QPL>
 __device__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* __restrict__ X,
                              const FitT* __restrict__ F, const uint32_t* perm, bool res, int t,
                              int r, int row)
 {
     const int lane = threadIdx.x & 31;
-    const int D = R.prob.D, Dp = R.prob.Dp, ps = R.ps;
+    const int D = R.prob.D, Dp = R.prob.Dp, ps = R.ps, np = R.np;
     const uint32_t seed = R.seed, run = R.run;
-    const uint4 sc = philox((uint32_t)t, (uint32_t)r, kAll, kSlotScal, seed, run);
-    const uint4 sc2 = philox((uint32_t)t, (uint32_t)r, kAll, kSlotScal2, seed, run);
+    // lane 0: SCAL, lane 1: SCAL2, lane 2 + k: PAIR k
+    uint32_t jslot = kSlotPair, jd = (uint32_t)(lane - 2);
+    if (lane == 0) { jslot = kSlotScal; jd = kAll; }
+    if (lane == 1) { jslot = kSlotScal2; jd = kAll; }
+    const uint4 jw = philox((uint32_t)t, (uint32_t)r, jd, jslot, seed, run);
+    uint4 sc, sc2;
+    sc.x = __shfl_sync(0xffffffffu, jw.x, 0); sc.y = __shfl_sync(0xffffffffu, jw.y, 0);
+    sc.z = __shfl_sync(0xffffffffu, jw.z, 0); sc.w = __shfl_sync(0xffffffffu, jw.w, 0);
+    sc2.x = __shfl_sync(0xffffffffu, jw.x, 1); sc2.y = __shfl_sync(0xffffffffu, jw.y, 1);
     const int W = (ps + 31) >> 5;
     const bool in_dr = (R.drmask[(size_t)t * W + (r >> 5)] >> (r & 31)) & 1u;
     const uint32_t mm = m24p1(sc.x);
     int mode;
     if (in_dr) mode = (mm < R.thr_dr[r]) ? kDormancy : kReproduction;
     else mode = (mm < R.thr_ah[t]) ? kAutotrophic : kHeterotrophic;
+    const bool forage = mode == kAutotrophic || mode == kHeterotrophic;
 
+    // rows from the snapshot: X_i, X_j (autotrophic) and the first pair
+    const int si = (int)perm[r];
+    int sj = si, sa = si, sb = si;
+    if (mode == kAutotrophic) {
+        sj = (int)perm[idx_draw(sc2.y, (uint32_t)ps)];
+        const uint32_t p0 = __shfl_sync(0xffffffffu, jw.x, 2), p1 = __shfl_sync(0xffffffffu, jw.y, 2);
+        sa = (int)perm[idx_draw(p0, (uint32_t)ps)];
+        sb = (int)perm[idx_draw(p1, (uint32_t)ps)];
+    } else if (mode == kHeterotrophic) {
+        sa = (int)perm[r - 1 < 0 ? 0 : r - 1];
+        sb = (int)perm[r + 1 > ps - 1 ? ps - 1 : r + 1];
+    }
+    float xi[2 * QPL], xj[2 * QPL], xa[2 * QPL], xb[2 * QPL];
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const int q = lane + 32 * j;
+        float2 vi = make_float2(0.f, 0.f), vj = vi, va = vi, vb = vi;
+        if (2 * q < D) {
+            vi = ldst(reinterpret_cast<const float2*>(X + (size_t)si * Dp) + q, res);
+            if (mode == kAutotrophic) vj = ldst(reinterpret_cast<const float2*>(X + (size_t)sj * Dp) + q, res);
+            if (forage) {
+                va = ldst(reinterpret_cast<const float2*>(X + (size_t)sa * Dp) + q, res);
+                vb = ldst(reinterpret_cast<const float2*>(X + (size_t)sb * Dp) + q, res);
+            }
+        }
+        xi[2 * j] = vi.x; xi[2 * j + 1] = vi.y;
+        xj[2 * j] = vj.x; xj[2 * j + 1] = vj.y;
+        xa[2 * j] = va.x; xa[2 * j + 1] = va.y;
+        xb[2 * j] = vb.x; xb[2 * j + 1] = vb.y;
+    }
+    float fa = 0.f, fb = 1.f;
+    if (forage) {
+        fa = (float)ldst(F + sa, res);
+        fb = (float)ldst(F + sb, res);
+    }
+
+    // per-dimension draws and the mask (independent of the gathered rows)
     uint32_t A[2 * QPL], B[2 * QPL];
     uint32_t valid = 0;
 #pragma unroll
@@ -456,74 +506,58 @@ __device__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* 
     if (mode == kReproduction) {
         const int k = (int)(((unsigned long long)D * m24p1(sc2.x) + 0xFFFFFFull) >> 24);
         mask = warp_kselect<QPL>(B, valid, k);
-    } else if (mode != kDormancy) {
+    } else if (forage) {
         const int k = (D * (r + 1) + ps - 1) / ps;
         mask = warp_kselect<QPL>(B, valid, k);
     }
 
-    // rows gathered from the snapshot
-    const int si = (int)perm[r];
-    float xi[2 * QPL], xa[2 * QPL], acc[2 * QPL];
+    // Eq. 7 / Eq. 10 weights and the pair sums
+    float acc[2 * QPL];
+    if (forage) {
+        const float w = expf(-fabsf(fa / (fb + kEps)));
 #pragma unroll
-    for (int j = 0; j < QPL; ++j) {
-        const int q = lane + 32 * j;
-        float2 v = make_float2(0.f, 0.f);
-        if (2 * q < D) v = ldst(reinterpret_cast<const float2*>(X + (size_t)si * Dp) + q, res);
-        xi[2 * j] = v.x;
-        xi[2 * j + 1] = v.y;
-        acc[2 * j] = acc[2 * j + 1] = 0.f;
-        xa[2 * j] = xa[2 * j + 1] = 0.f;
-    }
-    const float inv_np = 1.f / (float)R.np;
-    float ff = 0.f, s = 1.f;
-    if (mode == kAutotrophic || mode == kHeterotrophic) {
-        ff = u01(sc.y) * R.fsc[t];
-        for (int k = 1; k <= R.np; ++k) {
-            int a, b;
+        for (int e = 0; e < 2 * QPL; ++e) acc[e] = w * (xa[e] - xb[e]);
+        for (int k = 2; k <= np; ++k) {
             if (mode == kAutotrophic) {
-                const uint4 pr = philox((uint32_t)t, (uint32_t)r, (uint32_t)(k - 1), kSlotPair, seed, run);
-                a = (int)idx_draw(pr.x, (uint32_t)ps);
-                b = (int)idx_draw(pr.y, (uint32_t)ps);
+                uint32_t p0, p1;
+                if (k + 1 < 32) {
+                    p0 = __shfl_sync(0xffffffffu, jw.x, k + 1);
+                    p1 = __shfl_sync(0xffffffffu, jw.y, k + 1);
+                } else {
+                    const uint4 pr = philox((uint32_t)t, (uint32_t)r, (uint32_t)(k - 1), kSlotPair, seed, run);
+                    p0 = pr.x;
+                    p1 = pr.y;
+                }
+                sa = (int)perm[idx_draw(p0, (uint32_t)ps)];
+                sb = (int)perm[idx_draw(p1, (uint32_t)ps)];
             } else {
-                a = r - k < 0 ? 0 : r - k;
-                b = r + k > ps - 1 ? ps - 1 : r + k;
+                sa = (int)perm[r - k < 0 ? 0 : r - k];
+                sb = (int)perm[r + k > ps - 1 ? ps - 1 : r + k];
             }
-            const int sa = (int)perm[a], sb = (int)perm[b];
-            const float fa = (float)ldst(F + sa, res), fb = (float)ldst(F + sb, res);
-            const float w = expf(-fabsf(fa / (fb + kEps)));
+            const float w2 = expf(-fabsf((float)ldst(F + sa, res) / ((float)ldst(F + sb, res) + kEps)));
 #pragma unroll
             for (int j = 0; j < QPL; ++j) {
                 const int q = lane + 32 * j;
                 if (2 * q < D) {
                     const float2 va = ldst(reinterpret_cast<const float2*>(X + (size_t)sa * Dp) + q, res);
                     const float2 vb = ldst(reinterpret_cast<const float2*>(X + (size_t)sb * Dp) + q, res);
-                    acc[2 * j] = fmaf(w, va.x - vb.x, acc[2 * j]);
-                    acc[2 * j + 1] = fmaf(w, va.y - vb.y, acc[2 * j + 1]);
+                    acc[2 * j] = fmaf(w2, va.x - vb.x, acc[2 * j]);
+                    acc[2 * j + 1] = fmaf(w2, va.y - vb.y, acc[2 * j + 1]);
                 }
             }
         }
-        if (mode == kAutotrophic) {
-            const int jr = (int)idx_draw(sc2.y, (uint32_t)ps);
-            const int sj = (int)perm[jr];
+    } else {
 #pragma unroll
-            for (int j = 0; j < QPL; ++j) {
-                const int q = lane + 32 * j;
-                if (2 * q < D) {
-                    const float2 v = ldst(reinterpret_cast<const float2*>(X + (size_t)sj * Dp) + q, res);
-                    xa[2 * j] = v.x;
-                    xa[2 * j + 1] = v.y;
-                }
-            }
-        } else {
-            s = sign_draw(sc.z);
-        }
-    } else if (mode == kReproduction) {
-        s = sign_draw(sc.z);
+        for (int e = 0; e < 2 * QPL; ++e) acc[e] = 0.f;
     }
+    const float inv_np = 1.f / (float)np;
+    const float ff = forage ? u01(sc.y) * R.fsc[t] : 0.f;
+    const float s = sign_draw(sc.z);
     const float rho = u01(sc.w);
     const float nsc = R.nsc[t];
 
     float* xc = S.Xc + (size_t)row * Dp;
+    float* xo = S.Xo + (size_t)row * Dp;
 #pragma unroll
     for (int j = 0; j < QPL; ++j) {
         const int q = lane + 32 * j;
@@ -542,15 +576,17 @@ __device__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* 
                     if (mode == kReproduction) {
                         x = x0 + s * rho * fmaf(u01(A[sl]), ub - lb, lb);       // Eq. 2
                     } else if (mode == kAutotrophic) {
-                        x = x0 + ff * (xa[sl] - x0 + acc[sl] * inv_np);         // Eq. 6
+                        x = x0 + ff * (xj[sl] - x0 + acc[sl] * inv_np);         // Eq. 6
                     } else {
                         const float xnear = (1.f + s * u01(A[sl]) * nsc) * x0;  // Eq. 9
                         x = x0 + ff * (xnear - x0 + acc[sl] * inv_np);          // Eq. 8
                     }
                 }
                 xc[d] = fminf(fmaxf(x, lb), ub);
+                xo[d] = x0;
             } else if (d < Dp) {
                 xc[d] = 0.f;
+                xo[d] = 0.f;
             }
         }
     }
@@ -584,10 +620,11 @@ __device__ void run_one(const ApoRun& R, int local, unsigned char* smem, int* st
 {
     using KO = KeyOf<FitT>;
     using KT = typename KO::T;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const DevProblem& P = R.prob;
     const int D = P.D, Dp = P.Dp, ps = R.ps, g = R.g;
     const SmemPlan& L = R.plan;
+    const int CH = L.chunk;
     const Smem<FitT> S = carve<FitT>(smem, L);
     const bool res = L.resident != 0;
     unsigned bgen = 0;
@@ -607,12 +644,12 @@ __device__ void run_one(const ApoRun& R, int local, unsigned char* smem, int* st
     __syncthreads();
 
     if (R.flags & kFlagInit) {
-        for (int c0 = r0; c0 < r1; c0 += kChunk) {
-            const int rows = min(kChunk, r1 - c0);
-            for (int row = warp; row < rows; row += kWarps) gen_init_row<FitT, QPL>(R, S, c0 + row, row);
+        for (int c0 = r0; c0 < r1; c0 += CH) {
+            const int rows = min(CH, r1 - c0);
+            for (int row = warp; row < rows; row += nw) gen_init_row<FitT, QPL>(R, S, c0 + row, row);
             __syncthreads();
             eval_chunk<FitT>(R, S, rows);
-            for (int row = warp; row < rows; row += kWarps) {
+            for (int row = warp; row < rows; row += nw) {
                 float* dst = Xs[0] + (size_t)(c0 + row) * Dp;
                 for (int d = lane; d < Dp; d += 32) dst[d] = S.Xc[(size_t)row * Dp + d];
                 if (lane == 0) Fs[0][c0 + row] = S.rowF[row];
@@ -644,22 +681,21 @@ __device__ void run_one(const ApoRun& R, int local, unsigned char* smem, int* st
         perm = pnew;
         if (local == 0 && tid == 0 && R.curve) R.curve[t - 1] = (float)ldst(Fs[cur] + perm[0], res);
 
-        for (int c0 = r0; c0 < r1; c0 += kChunk) {
-            const int rows = min(kChunk, r1 - c0);
-            for (int row = warp; row < rows; row += kWarps)
+        for (int c0 = r0; c0 < r1; c0 += CH) {
+            const int rows = min(CH, r1 - c0);
+            for (int row = warp; row < rows; row += nw)
                 gen_step_row<FitT, QPL>(R, S, Xs[cur], Fs[cur], perm, res, t, c0 + row, row);
             __syncthreads();
             eval_chunk<FitT>(R, S, rows);
             // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i).
-            for (int row = warp; row < rows; row += kWarps) {
+            for (int row = warp; row < rows; row += nw) {
                 const int slot = (int)perm[c0 + row];
                 const FitT fo = ldst(Fs[cur] + slot, res);
                 const FitT fn = S.rowF[row];
                 const bool acc = fn < fo;
-                const float4* src = acc ? reinterpret_cast<const float4*>(S.Xc + (size_t)row * Dp)
-                                        : reinterpret_cast<const float4*>(Xs[cur] + (size_t)slot * Dp);
+                const float4* src = reinterpret_cast<const float4*>((acc ? S.Xc : S.Xo) + (size_t)row * Dp);
                 float4* dst = reinterpret_cast<float4*>(Xs[cur ^ 1] + (size_t)slot * Dp);
-                for (int v = lane; v < (Dp >> 2); v += 32) dst[v] = (acc || res) ? src[v] : __ldcg(src + v);
+                for (int v = lane; v < (Dp >> 2); v += 32) dst[v] = src[v];
                 if (lane == 0) Fs[cur ^ 1][slot] = acc ? fn : fo;
             }
             __syncthreads();
@@ -672,7 +708,7 @@ __device__ void run_one(const ApoRun& R, int local, unsigned char* smem, int* st
     if (R.flags & kFlagStepOut) {
         float* xo = R.X_out;
         FitT* fo = static_cast<FitT*>(R.F_out);
-        for (int r = r0 + warp; r < r1; r += kWarps) {
+        for (int r = r0 + warp; r < r1; r += nw) {
             const int slot = (int)perm[r];
             for (int d = lane; d < D; d += 32) xo[(size_t)r * D + d] = ldst(Xs[cur] + (size_t)slot * Dp + d, res);
             if (lane == 0) fo[r] = ldst(Fs[cur] + slot, res);
@@ -701,19 +737,11 @@ __device__ __forceinline__ void copy_run(ApoRun* dst, const ApoRun* src)
 
 template <typename FitT, int QPL>
 __global__ void __launch_bounds__(kThreads) run_kernel(const ApoRun* __restrict__ runs, int n_runs,
-                                                       int grid_g, int* queue, int* status)
+                                                       int* queue, int* status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ApoRun R;
     __shared__ int s_run, s_flag, s_int;
-    if (grid_g > 0) {
-        const int run = blockIdx.x / grid_g, local = blockIdx.x % grid_g;
-        if (run >= n_runs) return;
-        copy_run(&R, runs + run);
-        __syncthreads();
-        run_one<FitT, QPL>(R, local, smem, status, &s_flag, &s_int);
-        return;
-    }
     for (;;) {
         if (threadIdx.x == 0) s_run = atomicAdd(queue, 1);
         __syncthreads();
@@ -724,6 +752,178 @@ __global__ void __launch_bounds__(kThreads) run_kernel(const ApoRun* __restrict_
         run_one<FitT, QPL>(R, 0, smem, status, &s_flag, &s_int);
         __syncthreads();
     }
+}
+
+// ------------------------------------------------------------ grid mode
+// g CTAs run one optimisation run; CTA `local` owns the rank positions
+// [r0, r1) of every iteration and keeps a full copy of the rank -> slot
+// permutation in shared memory.  Per iteration:
+//   R1  sort the keys (F, previous rank) of the own rank range and publish
+//       them as a sorted segment of keys_g;                       barrier A
+//   R2  the new rank of each own key = its position in its own segment plus
+//       its lower bound in every other segment (the stable sort of
+//       Algorithm 1, distributed); scatter perm_g[rank] = slot;    barrier B
+//   R3  copy perm_g, then generate, evaluate and replace the own rank range;
+//       candidates read the double-buffered snapshot of the iteration.
+template <typename FitT>
+__device__ __forceinline__ int lower_bound_key(const typename KeyOf<FitT>::T* seg, int len,
+                                               typename KeyOf<FitT>::T k)
+{
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (KeyOf<FitT>::less(seg[mid], k)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename FitT, int QPL>
+__device__ void run_grid(const ApoRun& R, int local, unsigned char* smem, int* status, int* s_flag)
+{
+    using KO = KeyOf<FitT>;
+    using KT = typename KO::T;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int NT = blockDim.x;
+    const DevProblem& P = R.prob;
+    const int D = P.D, Dp = P.Dp, ps = R.ps, g = R.g;
+    const SmemPlan& L = R.plan;
+    const int CH = L.chunk;
+    const Smem<FitT> S = carve<FitT>(smem, L);
+    unsigned bgen = 0;
+
+    load_constants<FitT>(R, S);
+    float* Xs[2] = {R.X[0], R.X[1]};
+    FitT* Fs[2] = {static_cast<FitT*>(R.F[0]), static_cast<FitT*>(R.F[1])};
+    uint32_t* perm = S.perm[0];
+    int* rk = reinterpret_cast<int*>(S.perm[1]);
+    KT* keys = static_cast<KT*>(S.keys);
+    KT* keys_g = static_cast<KT*>(R.keys_g);
+    const int r0 = (int)((long long)ps * local / g);
+    const int r1 = (int)((long long)ps * (local + 1) / g);
+    const int nown = r1 - r0;
+    int npad = 1;
+    while (npad < nown) npad <<= 1;
+    for (int r = tid; r < ps; r += NT) perm[r] = (uint32_t)r;
+    __syncthreads();
+
+    if (R.flags & kFlagInit) {
+        for (int c0 = r0; c0 < r1; c0 += CH) {
+            const int rows = min(CH, r1 - c0);
+            for (int row = warp; row < rows; row += nw) gen_init_row<FitT, QPL>(R, S, c0 + row, row);
+            __syncthreads();
+            eval_chunk<FitT>(R, S, rows);
+            for (int row = warp; row < rows; row += nw) {
+                float* dst = Xs[0] + (size_t)(c0 + row) * Dp;
+                for (int d = lane; d < Dp; d += 32) dst[d] = S.Xc[(size_t)row * Dp + d];
+                if (lane == 0) Fs[0][c0 + row] = S.rowF[row];
+            }
+            __syncthreads();
+        }
+    }
+
+    int cur = 0;
+    const bool step_out = (R.flags & kFlagStepOut) != 0;
+    for (int t = R.t_begin;; ++t) {
+        // R1: own keys (F, rank in the current order), sorted and published
+        for (int i = tid; i < npad; i += NT)
+            keys[i] = i < nown ? KO::make(ldst(Fs[cur] + perm[r0 + i], false), (uint32_t)(r0 + i)) : KO::pad();
+        __syncthreads();
+        bitonic_sort<KO>(keys, npad);
+        for (int i = tid; i < nown; i += NT) keys_g[r0 + i] = keys[i];
+        if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
+
+        // the best of the population after iteration t - 1: the smallest head
+        if (local == 0) {
+            if (tid == 0) {
+                KT best = KO::pad();
+                for (int c = 0; c < g; ++c) {
+                    const int b = (int)((long long)ps * c / g);
+                    const int e = (int)((long long)ps * (c + 1) / g);
+                    if (e > b) {
+                        const KT h = __ldcg(keys_g + b);
+                        if (KO::less(h, best)) best = h;
+                    }
+                }
+                *reinterpret_cast<int*>(S.red) = (int)perm[KO::idx(best)];
+            }
+            __syncthreads();
+            const int bslot = *reinterpret_cast<int*>(S.red);
+            const FitT fb = ldst(Fs[cur] + bslot, false);
+            if (tid == 0 && R.curve) R.curve[t - 1] = (float)fb;
+            if (t > R.t_end && !step_out) {
+                if (tid == 0 && R.best_f) *R.best_f = (double)fb;
+                if (R.best_x)
+                    for (int d = tid; d < D; d += NT) R.best_x[d] = ldst(Xs[cur] + (size_t)bslot * Dp + d, false);
+            }
+        }
+        if (t > R.t_end) break;
+
+        // R2: distributed ranking
+        for (int i = tid; i < ps; i += NT) keys[i] = __ldcg(keys_g + i);
+        for (int i = tid; i < nown; i += NT) rk[i] = i;
+        __syncthreads();
+        for (int w = tid; w < nown * g; w += NT) {
+            const int i = w / g, c = w - i * g;
+            if (c == local) continue;
+            const int b = (int)((long long)ps * c / g);
+            const int e = (int)((long long)ps * (c + 1) / g);
+            const int lb = lower_bound_key<FitT>(keys + b, e - b, keys[r0 + i]);
+            if (lb) atomicAdd(&rk[i], lb);
+        }
+        __syncthreads();
+        for (int i = tid; i < nown; i += NT) R.perm_g[rk[i]] = perm[KO::idx(keys[r0 + i])];
+        if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
+
+        // R3: the new permutation, then the own rank range
+        for (int r = tid; r < ps; r += NT) perm[r] = __ldcg(R.perm_g + r);
+        __syncthreads();
+        for (int c0 = r0; c0 < r1; c0 += CH) {
+            const int rows = min(CH, r1 - c0);
+            for (int row = warp; row < rows; row += nw)
+                gen_step_row<FitT, QPL>(R, S, Xs[cur], Fs[cur], perm, false, t, c0 + row, row);
+            __syncthreads();
+            eval_chunk<FitT>(R, S, rows);
+            // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i).
+            for (int row = warp; row < rows; row += nw) {
+                const int slot = (int)perm[c0 + row];
+                const FitT fo = ldst(Fs[cur] + slot, false);
+                const FitT fn = S.rowF[row];
+                const bool acc = fn < fo;
+                const float4* src = reinterpret_cast<const float4*>((acc ? S.Xc : S.Xo) + (size_t)row * Dp);
+                float4* dst = reinterpret_cast<float4*>(Xs[cur ^ 1] + (size_t)slot * Dp);
+                for (int v = lane; v < (Dp >> 2); v += 32) dst[v] = src[v];
+                if (lane == 0) Fs[cur ^ 1][slot] = acc ? fn : fo;
+            }
+            __syncthreads();
+        }
+        cur ^= 1;
+        if (step_out && t == R.t_end) {
+            float* xo = R.X_out;
+            FitT* fo = static_cast<FitT*>(R.F_out);
+            for (int r = r0 + warp; r < r1; r += nw) {
+                const int slot = (int)perm[r];
+                for (int d = lane; d < D; d += 32) xo[(size_t)r * D + d] = ldst(Xs[cur] + (size_t)slot * Dp + d, false);
+                if (lane == 0) fo[r] = ldst(Fs[cur] + slot, false);
+            }
+            break;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename FitT, int QPL>
+__global__ void __launch_bounds__(kGridThreads, 1) grid_kernel(const ApoRun* __restrict__ runs, int n_runs,
+                                                                int grid_g, int* status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ApoRun R;
+    __shared__ int s_flag;
+    const int run = blockIdx.x / grid_g, local = blockIdx.x % grid_g;
+    if (run >= n_runs) return;
+    copy_run(&R, runs + run);
+    __syncthreads();
+    run_grid<FitT, QPL>(R, local, smem, status, &s_flag);
 }
 
 // ------------------------------------------------------- evaluation hook
@@ -740,9 +940,9 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const ApoRun* __restrict
     load_constants<FitT>(R, S);
     __syncthreads();
     const int D = R.prob.D, Dp = R.prob.Dp, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int c0 = blockIdx.x * kChunk; c0 < n; c0 += gridDim.x * kChunk) {
-        const int rows = min(kChunk, n - c0);
-        for (int row = warp; row < rows; row += kWarps) {
+    for (int c0 = blockIdx.x * R.plan.chunk; c0 < n; c0 += gridDim.x * R.plan.chunk) {
+        const int rows = min(R.plan.chunk, n - c0);
+        for (int row = warp; row < rows; row += (int)(blockDim.x >> 5)) {
             for (int d = lane; d < Dp; d += 32) {
                 float x = d < D ? X[(size_t)(c0 + row) * D + d] : 0.f;
                 if (select && d < D) x = fminf(fmaxf(x, S.lb[d]), S.ub[d]);
@@ -751,7 +951,7 @@ __global__ void __launch_bounds__(kThreads) eval_kernel(const ApoRun* __restrict
         }
         __syncthreads();
         eval_chunk<FitT>(R, S, rows);
-        for (int row = warp; row < rows; row += kWarps) {
+        for (int row = warp; row < rows; row += (int)(blockDim.x >> 5)) {
             const int i = c0 + row;
             const FitT fn = S.rowF[row];
             if (!select) {
@@ -808,15 +1008,18 @@ template <typename FitT, int QPL>
 static cudaError_t launch_run_t(const ApoRun* d_runs, int n_runs, int grid_g, int n_ctas, int* d_queue,
                                 int* d_status, size_t smem, cudaStream_t st)
 {
+    if (grid_g > 0) {
+        auto fn = grid_kernel<FitT, QPL>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        void* args[] = {(void*)&d_runs, (void*)&n_runs, (void*)&grid_g, (void*)&d_status};
+        return cudaLaunchCooperativeKernel((const void*)fn, dim3(n_runs * grid_g), dim3(kGridThreads), args,
+                                           smem, st);
+    }
     auto fn = run_kernel<FitT, QPL>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (grid_g > 0) {
-        void* args[] = {(void*)&d_runs, (void*)&n_runs, (void*)&grid_g, (void*)&d_queue, (void*)&d_status};
-        return cudaLaunchCooperativeKernel((const void*)fn, dim3(n_runs * grid_g), dim3(kThreads), args,
-                                           smem, st);
-    }
-    fn<<<n_ctas, kThreads, smem, st>>>(d_runs, n_runs, 0, d_queue, d_status);
+    fn<<<n_ctas, kThreads, smem, st>>>(d_runs, n_runs, d_queue, d_status);
     return cudaGetLastError();
 }
 
@@ -836,24 +1039,30 @@ cudaError_t launch_run(const ApoRun* d_runs, int n_runs, int grid_g, int n_ctas,
 }
 
 template <typename FitT, int QPL>
-static int capacity_t(size_t smem)
+static int capacity_t(size_t smem, bool grid)
 {
-    auto fn = run_kernel<FitT, QPL>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int per_sm = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess) return 0;
+    if (grid) {
+        auto fn = grid_kernel<FitT, QPL>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGridThreads, smem) != cudaSuccess) return 0;
+    } else {
+        auto fn = run_kernel<FitT, QPL>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess) return 0;
+    }
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return per_sm * sms;
 }
 
-int run_kernel_capacity(bool fit64, int qpl, size_t smem)
+int run_kernel_capacity(bool fit64, int qpl, size_t smem, bool grid)
 {
-    if (fit64) return qpl == 1 ? capacity_t<double, 1>(smem) : 0;
+    if (fit64) return qpl == 1 ? capacity_t<double, 1>(smem, grid) : 0;
     switch (qpl) {
-    case 1: return capacity_t<float, 1>(smem);
-    case 2: return capacity_t<float, 2>(smem);
-    case 4: return capacity_t<float, 4>(smem);
+    case 1: return capacity_t<float, 1>(smem, grid);
+    case 2: return capacity_t<float, 2>(smem, grid);
+    case 4: return capacity_t<float, 4>(smem, grid);
     default: return 0;
     }
 }

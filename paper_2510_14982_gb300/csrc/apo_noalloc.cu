@@ -24,6 +24,7 @@
 
 #include "../../include/apo.h"
 #include "apo_internal.h"
+#include "apo_plan.h"
 
 using namespace apo;
 
@@ -44,12 +45,6 @@ void* g_na_addr[kMaxDevices] = {};
 thread_local char g_na_err[256] = "";
 
 size_t al(size_t v, size_t a) { return (v + a - 1) / a * a; }
-int pow2(int v)
-{
-    int p = 1;
-    while (p < v) p <<= 1;
-    return p;
-}
 
 // Device address of the scratch array on the current device (looked up once).
 apo_status scratch_address(int dev, unsigned char** out)
@@ -71,50 +66,6 @@ apo_status scratch_address(int dev, unsigned char** out)
     }
     *out = static_cast<unsigned char*>(g_na_addr[dev]);
     return APO_OK;
-}
-
-// Shared-memory layout of the run (the same rules as the allocating path).
-SmemPlan plan_na(const apo_problem* P, int ps, bool resident, bool mt_smem)
-{
-    const bool fit64 = P->kind == APO_OBJ_OTSU;
-    const size_t fsz = fit64 ? 8 : 4;
-    const int Dp = P->Dp;
-    SmemPlan L;
-    std::memset(&L, 0, sizeof(L));
-    L.ps_pad = pow2(ps);
-    L.resident = resident;
-    L.mt_smem = mt_smem;
-    size_t off = 0;
-    auto take = [&](size_t bytes) -> uint32_t {
-        off = al(off, 16);
-        const uint32_t at = (uint32_t)off;
-        off += bytes;
-        return at;
-    };
-    L.X0 = take(resident ? (size_t)ps * Dp * 4 : 0);
-    L.X1 = take(resident ? (size_t)ps * Dp * 4 : 0);
-    L.F0 = take(resident ? ps * fsz : 0);
-    L.F1 = take(resident ? ps * fsz : 0);
-    L.perm0 = take((size_t)L.ps_pad * 4);
-    L.perm1 = take((size_t)L.ps_pad * 4);
-    L.keys = take((size_t)L.ps_pad * (fit64 ? 16 : 8));
-    L.MT = take(mt_smem ? (size_t)Dp * Dp * 4 : 0);
-    L.o = take(Dp * 4);
-    L.lb = take(Dp * 4);
-    L.ub = take(Dp * 4);
-    L.ew = take(Dp * 4);
-    L.Xc = take((size_t)kChunk * Dp * 4);
-    L.Yc = take((size_t)kChunk * Dp * 4);
-    L.Zc = take(P->any_rot ? (size_t)kChunk * Dp * 4 : 0);
-    L.rowF = take(kChunk * fsz);
-    L.compG = take(P->ncomp > 1 ? (size_t)kChunk * kMaxComp * 4 : 0);
-    L.compA = take(P->ncomp > 1 ? (size_t)kChunk * kMaxComp * 4 : 0);
-    L.P0 = take(fit64 ? 256 * 8 : 0);
-    L.P1 = take(fit64 ? 256 * 8 : 0);
-    L.otsu = take(fit64 ? kWarps * 32 * 4 : 0);
-    L.red = take((size_t)kThreads * 16);
-    L.total = (uint32_t)al(off, 16);
-    return L;
 }
 
 }  // namespace
@@ -142,10 +93,9 @@ extern "C" apo_status apo_run_device_noalloc(const apo_problem* P, const apo_par
     const int ps = p->ps, T = p->max_iter, Dp = P->Dp;
     const bool fit64 = P->kind == APO_OBJ_OTSU;
     const int qpl = fit64 ? 1 : (P->D <= 64 ? 1 : (P->D <= 128 ? 2 : 4));
-    const bool mts = P->ncomp == 1 && P->dev.comp[0].MT && (size_t)Dp * Dp * 4 <= 72 * 1024;
     const bool grid = ps > kQueueMaxPsNA;
-    SmemPlan plan = plan_na(P, ps, !grid, mts);
-    if (grid || plan.total > kSmemMaxNA) plan = plan_na(P, ps, false, mts);
+    SmemPlan plan = grid ? choose_plan(P, ps, false, true, kSmemMaxNA) : choose_plan(P, ps, true, false, kSmemMaxNA);
+    if (!grid && plan.total > kSmemMaxNA) plan = choose_plan(P, ps, false, false, kSmemMaxNA);
     if (plan.total > kSmemMaxNA) return fail(APO_ERR_UNSUPPORTED, "problem needs too much shared memory");
 
     // scratch layout
@@ -165,6 +115,7 @@ extern "C" apo_status apo_run_device_noalloc(const apo_problem* P, const apo_par
     const bool glob = !plan.resident;
     const size_t o_x0 = glob ? take((size_t)ps * Dp * 4) : 0, o_x1 = glob ? take((size_t)ps * Dp * 4) : 0;
     const size_t o_f0 = glob ? take(ps * fsz) : 0, o_f1 = glob ? take(ps * fsz) : 0;
+    const size_t o_pg = grid ? take((size_t)ps * 4) : 0, o_kg = grid ? take((size_t)ps * (fit64 ? 16 : 8)) : 0;
     if (off > kScratchBytes) {
         char msg[200];
         snprintf(msg, sizeof(msg), "this run needs %zu bytes of scratch; apo_run_device_noalloc is limited to "
@@ -189,7 +140,7 @@ extern "C" apo_status apo_run_device_noalloc(const apo_problem* P, const apo_par
 
     int g = 1;
     if (grid) {
-        const int cap = run_kernel_capacity(fit64, qpl, plan.total);
+        const int cap = run_kernel_capacity(fit64, qpl, plan.total, true);
         if (cap <= 0) return fail(APO_ERR_UNSUPPORTED, "grid kernel cannot be resident");
         g = std::max(1, std::min(cap, (ps + kGridMinRowsNA - 1) / kGridMinRowsNA));
     }
@@ -212,6 +163,10 @@ extern "C" apo_status apo_run_device_noalloc(const apo_problem* P, const apo_par
     }
     R.best_x = d_best_x; R.best_f = d_best_f; R.curve = d_curve;
     R.bar = reinterpret_cast<unsigned*>(base + o_ctrl + 16);
+    if (grid) {
+        R.perm_g = reinterpret_cast<uint32_t*>(base + o_pg);
+        R.keys_g = base + o_kg;
+    }
     const int offs[2] = {0, T};
     int* status = reinterpret_cast<int*>(base + o_ctrl);
     int* queue = reinterpret_cast<int*>(base + o_ctrl + 4);

@@ -1,0 +1,82 @@
+// apo_plan.h -- shared-memory layout of one run (host side), used by every
+// launching path so that the layout always matches the device carve().
+#pragma once
+
+#include <cstddef>
+#include <cstring>
+
+#include "apo_internal.h"
+
+namespace apo {
+
+inline size_t plan_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline int plan_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Layout for a run of population ps (0 for the evaluation hooks).  grid
+// selects the cooperative-grid layout (512 threads, 64-row chunks);
+// otherwise the resident / work-queue layout (256 threads, 32-row chunks).
+inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool mt_smem, bool grid)
+{
+    const bool fit64 = P->kind == 6;
+    const size_t fsz = fit64 ? 8 : 4;
+    const int Dp = P->Dp;
+    SmemPlan L;
+    std::memset(&L, 0, sizeof(L));
+    L.ps_pad = ps > 0 ? plan_pow2(ps) : 0;
+    L.resident = resident;
+    L.mt_smem = mt_smem;
+    L.chunk = grid ? kGridChunk : kChunk;
+    L.threads = grid ? kGridThreads : kThreads;
+    const size_t ch = (size_t)L.chunk;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> uint32_t {
+        off = plan_align(off, 16);
+        const uint32_t at = (uint32_t)off;
+        off += bytes;
+        return at;
+    };
+    L.X0 = take(resident ? (size_t)ps * Dp * 4 : 0);
+    L.X1 = take(resident ? (size_t)ps * Dp * 4 : 0);
+    L.F0 = take(resident ? ps * fsz : 0);
+    L.F1 = take(resident ? ps * fsz : 0);
+    L.perm0 = take((size_t)L.ps_pad * 4);
+    L.perm1 = take((size_t)L.ps_pad * 4);
+    L.keys = take((size_t)L.ps_pad * (fit64 ? 16 : 8));
+    L.MT = take(mt_smem ? (size_t)Dp * Dp * 4 : 0);
+    L.o = take(Dp * 4);
+    L.lb = take(Dp * 4);
+    L.ub = take(Dp * 4);
+    L.ew = take(Dp * 4);
+    L.Xc = take(ch * Dp * 4);
+    L.Xo = take(ch * Dp * 4);
+    L.Yc = take(ch * Dp * 4);
+    L.Zc = take(P->any_rot ? ch * Dp * 4 : 0);
+    L.rowF = take(ch * fsz);
+    L.compG = take(P->ncomp > 1 ? ch * kMaxComp * 4 : 0);
+    L.compA = take(P->ncomp > 1 ? ch * kMaxComp * 4 : 0);
+    L.P0 = take(fit64 ? 256 * 8 : 0);
+    L.P1 = take(fit64 ? 256 * 8 : 0);
+    L.otsu = take(fit64 ? kMaxWarps * 32 * 4 : 0);
+    L.red = take((size_t)L.threads * 16);
+    L.total = (uint32_t)plan_align(off, 16);
+    return L;
+}
+
+// The rotation of a single-component objective stays in shared memory when
+// the whole layout still fits.
+inline SmemPlan choose_plan(const apo_problem* P, int ps, bool resident, bool grid, size_t smem_max)
+{
+    const bool can = P->ncomp == 1 && P->dev.comp[0].MT;
+    if (can) {
+        SmemPlan L = make_smem_plan(P, ps, resident, true, grid);
+        if (L.total <= smem_max) return L;
+    }
+    return make_smem_plan(P, ps, resident, false, grid);
+}
+
+}  // namespace apo

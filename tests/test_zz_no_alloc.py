@@ -60,6 +60,6 @@ def test_noalloc_rejects_oversized_runs(apo):
     x = torch.zeros(100, device="cuda")
     f = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(apo.ApoError) as e:
-        apo.apo_run_device_noalloc(prob, apo.apo_params_make(8192, 1, 0.1, 3000, 0), x, f)
+        apo.apo_run_device_noalloc(prob, apo.apo_params_make(4096, 1, 0.1, 20000, 0), x, f)
     assert e.value.status == apo.APO_ERR_UNSUPPORTED
     assert "scratch" in str(e.value)
