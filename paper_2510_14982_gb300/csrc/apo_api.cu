@@ -159,6 +159,7 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
     }
 
     const int Dp = (D + 3) & ~3;
+    const int Np = (D + 15) & ~15;
     // Host image of every device array, laid out in one allocation.
     std::vector<std::pair<size_t, std::vector<unsigned char>>> pieces;
     size_t off = 0;
@@ -190,13 +191,13 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
         // MT[j][c] = M[perm[c]][j]; otherwise MT = M^T.
         const bool perm_rows = form == APO_OBJ_HYBRID;
         if (M || perm_rows) {
-            std::vector<float> mt((size_t)Dp * Dp, 0.f);
+            std::vector<float> mt((size_t)Dp * Np, 0.f);
             for (int c = 0; c < D; ++c) {
                 const int row = perm_rows ? perm[c] : c;
                 for (int j = 0; j < D; ++j)
-                    mt[(size_t)j * Dp + c] = M ? M[(size_t)row * D + j] : (j == row ? 1.f : 0.f);
+                    mt[(size_t)j * Np + c] = M ? M[(size_t)row * D + j] : (j == row ? 1.f : 0.f);
             }
-            off_mt[k] = add(mt.data(), (size_t)Dp * Dp * 4);
+            off_mt[k] = add(mt.data(), (size_t)Dp * Np * 4);
             has_mt[k] = true;
             any_rot = 1;
         }
@@ -245,7 +246,7 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
 
     apo_problem* P = new apo_problem();
     APO_CUDA(cudaGetDevice(&P->device));
-    P->D = D; P->Dp = Dp; P->kind = kind; P->ncomp = ncomp; P->any_rot = any_rot;
+    P->D = D; P->Dp = Dp; P->Np = Np; P->kind = kind; P->ncomp = ncomp; P->any_rot = any_rot;
     cudaError_t e = cudaMalloc(&P->mem, std::max<size_t>(off, 256));
     if (e != cudaSuccess) {
         delete P;
@@ -283,7 +284,7 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
     }
     DevProblem& dp = P->dev;
     std::memset(&dp, 0, sizeof(dp));
-    dp.D = D; dp.Dp = Dp; dp.kind = kind; dp.ncomp = ncomp;
+    dp.D = D; dp.Dp = Dp; dp.Np = Np; dp.kind = kind; dp.ncomp = ncomp;
     dp.lb = reinterpret_cast<const float*>(base + off_lb);
     dp.ub = reinterpret_cast<const float*>(base + off_ub);
     for (int k = 0; k < ncomp; ++k) {
@@ -570,7 +571,7 @@ apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
         // split into launches of at most `cap` runs (one CTA each at least)
         for (size_t i = 0; i < gr.runs.size(); i += (size_t)cap) {
             std::vector<int> sub(gr.runs.begin() + i, gr.runs.begin() + std::min(gr.runs.size(), i + (size_t)cap));
-            const int per = cap / (int)sub.size();
+            const int per = std::min(kMaxGridCtas, cap / (int)sub.size());
             for (int k : sub) {
                 const int want = (specs[k].prm.ps + kGridMinRows - 1) / kGridMinRows;
                 runs[k].g = std::max(1, std::min(per, want));

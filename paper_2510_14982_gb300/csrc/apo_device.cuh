@@ -17,6 +17,7 @@ constexpr int kMaxWarps = kGridThreads / 32;
 constexpr int kChunk = 32;        // candidate rows evaluated together (resident mode)
 constexpr int kGridChunk = 64;    // candidate rows evaluated together (grid mode)
 constexpr int kMaxComp = 10;      // composition components
+constexpr int kMaxGridCtas = 1024; // CTAs cooperating on one run (grid mode)
 
 // Counter slots of the Philox stream: counter = (iter, p, d, slot).
 constexpr uint32_t kSlotInit = 1;   // per (p, dim pair): initial population
@@ -40,7 +41,7 @@ constexpr int kFlagStepOut = 2;   // write the rank-ordered state to X_out / F_o
 // [0, s1) elliptic with weights ew, [s1, s2) Rosenbrock chain, [s2, D) Rastrigin.
 struct DevComp {
     const float* o;      // [Dp]
-    const float* MT;     // [Dp][Dp] transposed rotation, zero padded; nullptr = identity
+    const float* MT;     // [Dp][Np] transposed rotation, zero padded; nullptr = identity
     const float* ew;     // [Dp] elliptic weights of the first segment
     int s1, s2;
     float inv_2Dsig2;    // 1 / (2 D sigma^2) (composition)
@@ -48,7 +49,7 @@ struct DevComp {
 };
 
 struct DevProblem {
-    int D, Dp, kind, ncomp;
+    int D, Dp, Np, kind, ncomp;  // Dp = D rounded up to 4, Np = D rounded up to 16
     const float* lb;     // [Dp]
     const float* ub;     // [Dp]
     DevComp comp[kMaxComp];
@@ -64,7 +65,7 @@ struct SmemPlan {
     int chunk;           // candidate rows evaluated together
     int threads;         // CTA size the plan was made for
     uint32_t X0, X1, F0, F1, perm0, perm1, keys, MT, o, lb, ub, ew, Xc, Xo, Yc, Zc,
-        rowF, compG, compA, P0, P1, otsu, red, total;
+        rowF, compG, compA, P0, P1, otsu, red, seg, total;
 };
 
 struct ApoRun {

@@ -12,7 +12,7 @@
 // in one allocation `mem`, described by `dev`.
 struct apo_problem {
     int device;
-    int D, Dp, kind, ncomp;
+    int D, Dp, Np, kind, ncomp;
     int any_rot;
     apo::DevProblem dev;
     void* mem;

@@ -146,6 +146,7 @@ struct Smem {
     long long *P0, *P1;
     int* otsu;
     void* red;
+    int* seg;
 };
 
 template <typename FitT>
@@ -175,13 +176,14 @@ __device__ __forceinline__ Smem<FitT> carve(unsigned char* base, const SmemPlan&
     S.P1 = reinterpret_cast<long long*>(base + L.P1);
     S.otsu = reinterpret_cast<int*>(base + L.otsu);
     S.red = base + L.red;
+    S.seg = reinterpret_cast<int*>(base + L.seg);
     return S;
 }
 
 // Loads the run's constant vectors (and the rotation of a single-component
 // objective when it fits) into shared memory.
 template <typename FitT>
-__device__ void load_constants(const ApoRun& R, const Smem<FitT>& S)
+__device__ __forceinline__ void load_constants(const ApoRun& R, const Smem<FitT>& S)
 {
     const DevProblem& P = R.prob;
     const int Dp = P.Dp;
@@ -195,7 +197,7 @@ __device__ void load_constants(const ApoRun& R, const Smem<FitT>& S)
     if (R.plan.mt_smem && C.MT) {
         const float4* src = reinterpret_cast<const float4*>(C.MT);
         float4* dst = reinterpret_cast<float4*>(S.MT);
-        for (int i = threadIdx.x; i < Dp * Dp / 4; i += blockDim.x) dst[i] = src[i];
+        for (int i = threadIdx.x; i < Dp * P.Np / 4; i += blockDim.x) dst[i] = src[i];
     }
     if (P.kind == kOtsu) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) {
@@ -206,60 +208,89 @@ __device__ void load_constants(const ApoRun& R, const Smem<FitT>& S)
 }
 
 // ------------------------------------------------------------ evaluation
-// Zc[rows][Dp] = Yc[rows][Dp] * MT[Dp][Dp] (both zero padded beyond D):
-// FP32 FMA with 4 x 4 register tiles over the CTA.
-__device__ void tile_gemm(const float* __restrict__ Y, const float* __restrict__ MT,
-                          float* __restrict__ Z, int rows, int Dp)
+// 16-byte shared-memory load through an explicit shared-window address.
+__device__ __forceinline__ float4 lds4(uint32_t addr)
 {
-    const int ct = Dp >> 2;
-    const int rt = (rows + 3) >> 2;
-    for (int tile = threadIdx.x; tile < rt * ct; tile += blockDim.x) {
+    float4 v;
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
+
+// Z[rows][Np] = Y[rows][Dp] * MT[Dp][Np] with Y stored transposed (YT[k][row],
+// row stride CH) and both operands zero padded beyond D.  FP32 FMA.  A warp
+// computes an 8-row x 128-column tile, lane L the columns 4L..4L+3 of the 8
+// rows: per k the 8 row values are two broadcast 16-byte loads shared by the
+// whole warp and the columns one 16-byte load per lane.  MT_SHARED selects a
+// rotation held in shared memory (explicit ld.shared) or read through L1.
+template <bool MT_SHARED, int TR>
+__device__ __forceinline__ void tile_gemm_t(const float* __restrict__ YT, const float* __restrict__ MT,
+                                            float* __restrict__ Z, int rows, int Dp, int Np, int CH)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int rt = (rows + TR - 1) / TR, ct = (Np + 127) >> 7;
+    const uint32_t yt_s = (uint32_t)__cvta_generic_to_shared(YT);
+    const uint32_t mt_s = MT_SHARED ? (uint32_t)__cvta_generic_to_shared(MT) : 0u;
+    for (int tile = warp; tile < rt * ct; tile += nw) {
         const int tr = tile / ct, tc = tile - tr * ct;
-        const float* y0 = Y + (size_t)(4 * tr) * Dp;
-        float acc[4][4];
+        const int rb = TR * tr, c = 128 * tc + 4 * lane;
+        const bool col_ok = c < Np;
+        float acc[TR][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TR; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        for (int k = 0; k < Dp; k += 4) {
-            float4 a[4], b[4];
+#pragma unroll 2
+        for (int k = 0; k < Dp; ++k) {
+            const uint32_t ya = yt_s + 4u * (uint32_t)(k * CH + rb);
+            const float4 a0 = lds4(ya);
+            const float4 a1 = TR == 8 ? lds4(ya + 16u) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (col_ok) {
+                if (MT_SHARED) b = lds4(mt_s + 4u * (uint32_t)(k * Np + c));
+                else b = __ldg(reinterpret_cast<const float4*>(MT + (size_t)k * Np + c));
+            }
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(y0 + (size_t)i * Dp + k);
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                b[kk] = *reinterpret_cast<const float4*>(MT + (size_t)(k + kk) * Dp + 4 * tc);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float av[4] = {a[i].x, a[i].y, a[i].z, a[i].w};
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    acc[i][0] = fmaf(av[kk], b[kk].x, acc[i][0]);
-                    acc[i][1] = fmaf(av[kk], b[kk].y, acc[i][1]);
-                    acc[i][2] = fmaf(av[kk], b[kk].z, acc[i][2]);
-                    acc[i][3] = fmaf(av[kk], b[kk].w, acc[i][3]);
-                }
+            for (int i = 0; i < TR; ++i) {
+                acc[i][0] = fmaf(av[i], b.x, acc[i][0]);
+                acc[i][1] = fmaf(av[i], b.y, acc[i][1]);
+                acc[i][2] = fmaf(av[i], b.z, acc[i][2]);
+                acc[i][3] = fmaf(av[i], b.w, acc[i][3]);
             }
         }
+        if (col_ok) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-            *reinterpret_cast<float4*>(Z + (size_t)(4 * tr + i) * Dp + 4 * tc) =
-                make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            for (int i = 0; i < TR; ++i)
+                if (rb + i < rows)
+                    *reinterpret_cast<float4*>(Z + (size_t)(rb + i) * Np + c) =
+                        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        }
     }
 }
 
-// Segmented objective of one row by one warp: [0, s1) high-conditioned
+// 8-row tiles when they keep every warp busy, 4-row tiles otherwise.
+template <bool MT_SHARED>
+__device__ __forceinline__ void tile_gemm(const float* __restrict__ YT, const float* __restrict__ MT,
+                                          float* __restrict__ Z, int rows, int Dp, int Np, int CH)
+{
+    const int nw = blockDim.x >> 5, ct = (Np + 127) >> 7;
+    if (((rows + 7) >> 3) * ct >= nw) tile_gemm_t<MT_SHARED, 8>(YT, MT, Z, rows, Dp, Np, CH);
+    else tile_gemm_t<MT_SHARED, 4>(YT, MT, Z, rows, Dp, Np, CH);
+}
+
+// Segmented objective of one row by one warp (z[d * zs]): [0, s1) high-conditioned
 // elliptic, [s1, s2) chained Rosenbrock, [s2, D) Rastrigin cosine sum.
-__device__ float seg_value(const float* z, const DevComp& C, const float* ew, int D)
+__device__ __forceinline__ float seg_value(const float* z, int zs, const DevComp& C, const float* ew, int D)
 {
     const int lane = threadIdx.x & 31;
     float s = 0.f;
     for (int d = lane; d < D; d += 32) {
-        const float v = z[d];
+        const float v = z[(size_t)d * zs];
         if (d < C.s1) {
             s = fmaf(ew[d] * v, v, s);
         } else if (d < C.s2) {
             if (d + 1 < C.s2) {
-                const float a = z[d + 1] - v * v;
+                const float a = z[(size_t)(d + 1) * zs] - v * v;
                 const float b = v - 1.f;
                 s += 100.f * a * a + b * b;
             }
@@ -274,7 +305,7 @@ __device__ float seg_value(const float* z, const DevComp& C, const float* ew, in
 // 0..T-1), negated.  The float64 operations follow a fixed order with
 // explicit round-to-nearest intrinsics (no contraction) so that the value is
 // reproducible bit for bit.
-__device__ double otsu_row(const float* x, int T, const long long* P0, const long long* P1,
+__device__ __forceinline__ double otsu_row(const float* x, int T, const long long* P0, const long long* P1,
                            int* scratch)
 {
     const int lane = threadIdx.x & 31;
@@ -323,7 +354,7 @@ __device__ double otsu_row(const float* x, int T, const long long* P0, const lon
 // Evaluates the candidate rows Xc[0, rows) into rowF.  Called by the whole
 // CTA; ends synchronised.
 template <typename FitT>
-__device__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S, int rows)
+__device__ __forceinline__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S, int rows)
 {
     const DevProblem& P = R.prob;
     const int D = P.D, Dp = P.Dp;
@@ -336,30 +367,31 @@ __device__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S, int rows)
         __syncthreads();
         return;
     }
+    const int CH = R.plan.chunk, Np = P.Np;
     for (int c = 0; c < P.ncomp; ++c) {
         const DevComp& C = P.comp[c];
         const float* o = (c == 0) ? S.o : C.o;
-        for (int i = threadIdx.x; i < rows * Dp; i += blockDim.x) {
-            const int d = i % Dp;
-            S.Yc[i] = d < D ? S.Xc[i] - o[d] : 0.f;
+        // YT[d][row] = x - o (zero beyond D)
+        for (int i = threadIdx.x; i < CH * Dp; i += blockDim.x) {
+            const int d = i / CH, row = i - d * CH;
+            S.Yc[i] = (d < D && row < rows) ? S.Xc[(size_t)row * Dp + d] - o[d] : 0.f;
         }
         __syncthreads();
-        const float* Z = S.Yc;
         if (C.MT) {
-            const float* MT = (c == 0 && R.plan.mt_smem) ? S.MT : C.MT;
-            tile_gemm(S.Yc, MT, S.Zc, rows, Dp);
-            Z = S.Zc;
+            if (c == 0 && R.plan.mt_smem) tile_gemm<true>(S.Yc, S.MT, S.Zc, rows, Dp, Np, CH);
+            else tile_gemm<false>(S.Yc, C.MT, S.Zc, rows, Dp, Np, CH);
             __syncthreads();
         }
         const float* ew = (c == 0) ? S.ew : C.ew;
         for (int row = warp; row < rows; row += nw) {
-            const float v = seg_value(Z + (size_t)row * Dp, C, ew, D);
+            const float v = C.MT ? seg_value(S.Zc + (size_t)row * Np, 1, C, ew, D)
+                                 : seg_value(S.Yc + row, CH, C, ew, D);
             if (P.ncomp == 1) {
                 if (lane == 0) S.rowF[row] = (FitT)v;
             } else {
                 float d2 = 0.f;
                 for (int d = lane; d < D; d += 32) {
-                    const float y = S.Yc[(size_t)row * Dp + d];
+                    const float y = S.Yc[(size_t)d * CH + row];
                     d2 = fmaf(y, y, d2);
                 }
                 d2 = warp_sum(d2);
@@ -397,7 +429,7 @@ __device__ __forceinline__ T ldst(const T* p, bool resident)
 // ------------------------------------------------- candidate generation
 // Population initialisation (Algorithm 1): X_p = Xmin + U (Xmax - Xmin).
 template <typename FitT, int QPL>
-__device__ void gen_init_row(const ApoRun& R, const Smem<FitT>& S, int p, int row)
+__device__ __forceinline__ void gen_init_row(const ApoRun& R, const Smem<FitT>& S, int p, int row)
 {
     const int lane = threadIdx.x & 31;
     const int D = R.prob.D, Dp = R.prob.Dp;
@@ -427,7 +459,7 @@ __device__ void gen_init_row(const ApoRun& R, const Smem<FitT>& S, int p, int ro
 // requested before the per-dimension draws and the mask selection so that
 // their latency overlaps that arithmetic.
 template <typename FitT, int QPL>
-__device__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* __restrict__ X,
+__device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* __restrict__ X,
                              const FitT* __restrict__ F, const uint32_t* perm, bool res, int t,
                              int r, int row)
 {
@@ -486,6 +518,7 @@ __device__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* 
         fa = (float)ldst(F + sa, res);
         fb = (float)ldst(F + sb, res);
     }
+    if (lane == 0) S.rowF[R.plan.chunk + row] = ldst(F + si, res);   // old fitness for the greedy step
 
     // per-dimension draws and the mask (independent of the gathered rows)
     uint32_t A[2 * QPL], B[2 * QPL];
@@ -594,7 +627,7 @@ __device__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* 
 
 // -------------------------------------------------------------- the run
 template <typename FitT>
-__device__ void find_best(const Smem<FitT>& S, const FitT* F, const uint32_t* perm, int ps,
+__device__ __forceinline__ void find_best(const Smem<FitT>& S, const FitT* F, const uint32_t* perm, int ps,
                           bool res, typename KeyOf<FitT>::T* red, int* out_rank)
 {
     using KO = KeyOf<FitT>;
@@ -615,7 +648,7 @@ __device__ void find_best(const Smem<FitT>& S, const FitT* F, const uint32_t* pe
 }
 
 template <typename FitT, int QPL>
-__device__ void run_one(const ApoRun& R, int local, unsigned char* smem, int* status, int* s_flag,
+__device__ __forceinline__ void run_one(const ApoRun& R, int local, unsigned char* smem, int* status, int* s_flag,
                         int* s_int)
 {
     using KO = KeyOf<FitT>;
@@ -690,7 +723,7 @@ __device__ void run_one(const ApoRun& R, int local, unsigned char* smem, int* st
             // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i).
             for (int row = warp; row < rows; row += nw) {
                 const int slot = (int)perm[c0 + row];
-                const FitT fo = ldst(Fs[cur] + slot, res);
+                const FitT fo = S.rowF[CH + row];
                 const FitT fn = S.rowF[row];
                 const bool acc = fn < fo;
                 const float4* src = reinterpret_cast<const float4*>((acc ? S.Xc : S.Xo) + (size_t)row * Dp);
@@ -736,7 +769,7 @@ __device__ __forceinline__ void copy_run(ApoRun* dst, const ApoRun* src)
 }
 
 template <typename FitT, int QPL>
-__global__ void __launch_bounds__(kThreads) run_kernel(const ApoRun* __restrict__ runs, int n_runs,
+__global__ void __launch_bounds__(kThreads, 2) run_kernel(const ApoRun* __restrict__ runs, int n_runs,
                                                        int* queue, int* status)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -765,21 +798,66 @@ __global__ void __launch_bounds__(kThreads) run_kernel(const ApoRun* __restrict_
 //       Algorithm 1, distributed); scatter perm_g[rank] = slot;    barrier B
 //   R3  copy perm_g, then generate, evaluate and replace the own rank range;
 //       candidates read the double-buffered snapshot of the iteration.
+__device__ __forceinline__ unsigned long long lds_key(uint32_t a, unsigned long long*)
+{
+    unsigned long long v;
+    asm("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ ulonglong2 lds_key(uint32_t a, ulonglong2*)
+{
+    ulonglong2 v;
+    asm("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(a));
+    return v;
+}
+
+// Number of keys of the sorted shared-memory segment seg[0, len) below k.
 template <typename FitT>
 __device__ __forceinline__ int lower_bound_key(const typename KeyOf<FitT>::T* seg, int len,
                                                typename KeyOf<FitT>::T k)
 {
+    using KT = typename KeyOf<FitT>::T;
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(seg);
     int lo = 0, hi = len;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (KeyOf<FitT>::less(seg[mid], k)) lo = mid + 1;
+        if (KeyOf<FitT>::less(lds_key(base + (uint32_t)(mid * sizeof(KT)), (KT*)nullptr), k)) lo = mid + 1;
         else hi = mid;
     }
     return lo;
 }
 
+__device__ __forceinline__ unsigned long long shfl_xor_key(unsigned long long v, int m)
+{
+    return __shfl_xor_sync(0xffffffffu, v, m);
+}
+__device__ __forceinline__ ulonglong2 shfl_xor_key(ulonglong2 v, int m)
+{
+    return make_ulonglong2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// Copies n elements from global (L2, bypassing L1) to shared memory with
+// eight independent loads in flight per thread.
+template <typename T>
+__device__ __forceinline__ void copy_cg(T* dst, const T* __restrict__ src, int n)
+{
+    for (int base = threadIdx.x; base < n; base += 8 * blockDim.x) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = base + u * blockDim.x;
+            if (i < n) v[u] = __ldcg(src + i);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = base + u * blockDim.x;
+            if (i < n) dst[i] = v[u];
+        }
+    }
+}
+
 template <typename FitT, int QPL>
-__device__ void run_grid(const ApoRun& R, int local, unsigned char* smem, int* status, int* s_flag)
+__device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned char* smem, int* status, int* s_flag)
 {
     using KO = KeyOf<FitT>;
     using KT = typename KO::T;
@@ -796,9 +874,10 @@ __device__ void run_grid(const ApoRun& R, int local, unsigned char* smem, int* s
     float* Xs[2] = {R.X[0], R.X[1]};
     FitT* Fs[2] = {static_cast<FitT*>(R.F[0]), static_cast<FitT*>(R.F[1])};
     uint32_t* perm = S.perm[0];
-    int* rk = reinterpret_cast<int*>(S.perm[1]);
     KT* keys = static_cast<KT*>(S.keys);
     KT* keys_g = static_cast<KT*>(R.keys_g);
+    int* seg = S.seg;   // seg[c] = first rank position of CTA c; seg[g] = ps
+    for (int c = tid; c <= g; c += NT) seg[c] = (int)((long long)ps * c / g);
     const int r0 = (int)((long long)ps * local / g);
     const int r1 = (int)((long long)ps * (local + 1) / g);
     const int nown = r1 - r0;
@@ -823,29 +902,47 @@ __device__ void run_grid(const ApoRun& R, int local, unsigned char* smem, int* s
     }
 
     int cur = 0;
+    bool keys_ready = false;   // the greedy step already wrote the own keys
     const bool step_out = (R.flags & kFlagStepOut) != 0;
     for (int t = R.t_begin;; ++t) {
         // R1: own keys (F, rank in the current order), sorted and published
-        for (int i = tid; i < npad; i += NT)
-            keys[i] = i < nown ? KO::make(ldst(Fs[cur] + perm[r0 + i], false), (uint32_t)(r0 + i)) : KO::pad();
+        if (!keys_ready)
+            for (int i = tid; i < nown; i += NT)
+                keys[i] = KO::make(ldst(Fs[cur] + perm[r0 + i], false), (uint32_t)(r0 + i));
         __syncthreads();
-        bitonic_sort<KO>(keys, npad);
-        for (int i = tid; i < nown; i += NT) keys_g[r0 + i] = keys[i];
+        if (nown <= 2 * NT) {
+            // rank by counting among the own keys (all distinct)
+            for (int i = tid; i < nown; i += NT) {
+                const KT k = keys[i];
+                int rk = 0;
+                for (int j = 0; j < nown; ++j) rk += KO::less(keys[j], k) ? 1 : 0;
+                keys_g[r0 + rk] = k;
+            }
+        } else {
+            for (int i = tid; i < npad; i += NT)
+                if (i >= nown) keys[i] = KO::pad();
+            __syncthreads();
+            bitonic_sort<KO>(keys, npad);
+            for (int i = tid; i < nown; i += NT) keys_g[r0 + i] = keys[i];
+        }
         if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
 
         // the best of the population after iteration t - 1: the smallest head
         if (local == 0) {
-            if (tid == 0) {
+            if (warp == 0) {
                 KT best = KO::pad();
-                for (int c = 0; c < g; ++c) {
-                    const int b = (int)((long long)ps * c / g);
-                    const int e = (int)((long long)ps * (c + 1) / g);
-                    if (e > b) {
-                        const KT h = __ldcg(keys_g + b);
+                for (int c = lane; c < g; c += 32) {
+                    if (seg[c + 1] > seg[c]) {
+                        const KT h = __ldcg(keys_g + seg[c]);
                         if (KO::less(h, best)) best = h;
                     }
                 }
-                *reinterpret_cast<int*>(S.red) = (int)perm[KO::idx(best)];
+#pragma unroll
+                for (int m = 16; m; m >>= 1) {
+                    const KT o = shfl_xor_key(best, m);
+                    if (KO::less(o, best)) best = o;
+                }
+                if (lane == 0) *reinterpret_cast<int*>(S.red) = (int)perm[KO::idx(best)];
             }
             __syncthreads();
             const int bslot = *reinterpret_cast<int*>(S.red);
@@ -859,24 +956,22 @@ __device__ void run_grid(const ApoRun& R, int local, unsigned char* smem, int* s
         }
         if (t > R.t_end) break;
 
-        // R2: distributed ranking
-        for (int i = tid; i < ps; i += NT) keys[i] = __ldcg(keys_g + i);
-        for (int i = tid; i < nown; i += NT) rk[i] = i;
+        // R2: distributed ranking -- new rank = position in the own segment +
+        // lower bound in every other segment (one warp per key, lanes over segments)
+        copy_cg(keys, keys_g, ps);
         __syncthreads();
-        for (int w = tid; w < nown * g; w += NT) {
-            const int i = w / g, c = w - i * g;
-            if (c == local) continue;
-            const int b = (int)((long long)ps * c / g);
-            const int e = (int)((long long)ps * (c + 1) / g);
-            const int lb = lower_bound_key<FitT>(keys + b, e - b, keys[r0 + i]);
-            if (lb) atomicAdd(&rk[i], lb);
+        for (int i = warp; i < nown; i += nw) {
+            const KT k = keys[r0 + i];
+            int cnt = 0;
+            for (int c = lane; c < g; c += 32)
+                if (c != local) cnt += lower_bound_key<FitT>(keys + seg[c], seg[c + 1] - seg[c], k);
+            cnt = __reduce_add_sync(0xffffffffu, cnt) + i;
+            if (lane == 0) R.perm_g[cnt] = perm[KO::idx(k)];
         }
-        __syncthreads();
-        for (int i = tid; i < nown; i += NT) R.perm_g[rk[i]] = perm[KO::idx(keys[r0 + i])];
         if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
 
         // R3: the new permutation, then the own rank range
-        for (int r = tid; r < ps; r += NT) perm[r] = __ldcg(R.perm_g + r);
+        copy_cg(perm, R.perm_g, ps);
         __syncthreads();
         for (int c0 = r0; c0 < r1; c0 += CH) {
             const int rows = min(CH, r1 - c0);
@@ -884,19 +979,24 @@ __device__ void run_grid(const ApoRun& R, int local, unsigned char* smem, int* s
                 gen_step_row<FitT, QPL>(R, S, Xs[cur], Fs[cur], perm, false, t, c0 + row, row);
             __syncthreads();
             eval_chunk<FitT>(R, S, rows);
-            // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i).
+            // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i);
+            // the kept fitness also forms the own sort key of the next iteration.
             for (int row = warp; row < rows; row += nw) {
                 const int slot = (int)perm[c0 + row];
-                const FitT fo = ldst(Fs[cur] + slot, false);
+                const FitT fo = S.rowF[CH + row];
                 const FitT fn = S.rowF[row];
                 const bool acc = fn < fo;
                 const float4* src = reinterpret_cast<const float4*>((acc ? S.Xc : S.Xo) + (size_t)row * Dp);
                 float4* dst = reinterpret_cast<float4*>(Xs[cur ^ 1] + (size_t)slot * Dp);
                 for (int v = lane; v < (Dp >> 2); v += 32) dst[v] = src[v];
-                if (lane == 0) Fs[cur ^ 1][slot] = acc ? fn : fo;
+                if (lane == 0) {
+                    Fs[cur ^ 1][slot] = acc ? fn : fo;
+                    keys[c0 + row - r0] = KO::make(acc ? fn : fo, (uint32_t)(c0 + row));
+                }
             }
             __syncthreads();
         }
+        keys_ready = true;
         cur ^= 1;
         if (step_out && t == R.t_end) {
             float* xo = R.X_out;

@@ -142,7 +142,7 @@ extern "C" apo_status apo_run_device_noalloc(const apo_problem* P, const apo_par
     if (grid) {
         const int cap = run_kernel_capacity(fit64, qpl, plan.total, true);
         if (cap <= 0) return fail(APO_ERR_UNSUPPORTED, "grid kernel cannot be resident");
-        g = std::max(1, std::min(cap, (ps + kGridMinRowsNA - 1) / kGridMinRowsNA));
+        g = std::max(1, std::min(std::min(cap, kMaxGridCtas), (ps + kGridMinRowsNA - 1) / kGridMinRowsNA));
     }
     ApoRun R;
     std::memset(&R, 0, sizeof(R));

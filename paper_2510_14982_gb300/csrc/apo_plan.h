@@ -24,7 +24,7 @@ inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool
 {
     const bool fit64 = P->kind == 6;
     const size_t fsz = fit64 ? 8 : 4;
-    const int Dp = P->Dp;
+    const int Dp = P->Dp, Np = P->Np;
     SmemPlan L;
     std::memset(&L, 0, sizeof(L));
     L.ps_pad = ps > 0 ? plan_pow2(ps) : 0;
@@ -47,22 +47,23 @@ inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool
     L.perm0 = take((size_t)L.ps_pad * 4);
     L.perm1 = take((size_t)L.ps_pad * 4);
     L.keys = take((size_t)L.ps_pad * (fit64 ? 16 : 8));
-    L.MT = take(mt_smem ? (size_t)Dp * Dp * 4 : 0);
+    L.MT = take(mt_smem ? (size_t)Dp * Np * 4 : 0);
     L.o = take(Dp * 4);
     L.lb = take(Dp * 4);
     L.ub = take(Dp * 4);
     L.ew = take(Dp * 4);
     L.Xc = take(ch * Dp * 4);
     L.Xo = take(ch * Dp * 4);
-    L.Yc = take(ch * Dp * 4);
-    L.Zc = take(P->any_rot ? ch * Dp * 4 : 0);
-    L.rowF = take(ch * fsz);
+    L.Yc = take(ch * Dp * 4);                          // transposed: [Dp][chunk]
+    L.Zc = take(P->any_rot ? ch * Np * 4 : 0);          // [chunk][Np]
+    L.rowF = take(2 * ch * fsz);   // new fitness | old fitness of the chunk rows
     L.compG = take(P->ncomp > 1 ? ch * kMaxComp * 4 : 0);
     L.compA = take(P->ncomp > 1 ? ch * kMaxComp * 4 : 0);
     L.P0 = take(fit64 ? 256 * 8 : 0);
     L.P1 = take(fit64 ? 256 * 8 : 0);
     L.otsu = take(fit64 ? kMaxWarps * 32 * 4 : 0);
     L.red = take((size_t)L.threads * 16);
+    L.seg = take(grid ? (size_t)(kMaxGridCtas + 1) * 4 : 0);
     L.total = (uint32_t)plan_align(off, 16);
     return L;
 }
