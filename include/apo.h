@@ -153,6 +153,36 @@ apo_status apo_run_batch(const apo_problem* const* probs, const apo_params* para
                          void* stream, float* d_best_x, int x_stride, double* d_best_f,
                          float* d_curves, int curve_stride);
 
+/* A prepared batch: apo_run_batch split into a planning call and a launch
+ * call.  apo_batch_create plans the launches, allocates the workspace and
+ * uploads the run descriptors (synchronous); apo_batch_launch then only clears
+ * control words and launches the kernels (stream-ordered, no allocation, no
+ * host copy), so that it can be captured in a CUDA graph and replayed.  Every
+ * launch recomputes the runs from their initial populations: same params,
+ * same results.  Outputs are the caller's device buffers given at creation
+ * (layout as in apo_run_batch).  Launches of one batch must not overlap on
+ * the GPU (they share the workspace). */
+typedef struct apo_batch apo_batch;
+
+typedef struct apo_batch_options {
+    size_t smem_budget;   /* shared memory per work-queue CTA (bytes); 0 = the maximum.
+                             Runs whose population fits stay resident in shared memory,
+                             the others keep it in global memory.                     */
+    int ctas_per_sm;      /* work-queue CTAs per SM; 0 = as many as fit                */
+} apo_batch_options;
+
+apo_status apo_batch_create(const apo_problem* const* probs, const apo_params* params, int n_runs,
+                            float* d_best_x, int x_stride, double* d_best_f, float* d_curves,
+                            int curve_stride, const apo_batch_options* opt, apo_batch** out);
+apo_status apo_batch_launch(apo_batch* batch, void* stream);
+
+/* Autotuner: times the batch, truncated to its first `probe_iters`
+ * iterations, under candidate work-queue configurations (shared-memory
+ * budgets for 1, 2, 3 and 4 CTAs per SM), keeps the fastest and re-plans the
+ * batch with it.  Writes the choice to *chosen when not NULL.  Synchronous. */
+apo_status apo_batch_autotune(apo_batch* batch, void* stream, int probe_iters, apo_batch_options* chosen);
+void apo_batch_destroy(apo_batch* batch);
+
 /* Test hook: iteration `iter` (1..max_iter) of Algorithm 1 applied to a given
  * state.  d_X [ps*D] and d_F [ps] hold the population in its current order;
  * on return they hold it in the rank order of this iteration's fitness sort

@@ -28,7 +28,8 @@ APO_OK, APO_ERR_INVALID_ARG, APO_ERR_CUDA, APO_ERR_OOM, APO_ERR_TIMEOUT, APO_ERR
 # every entry point declared in include/apo.h
 EXPORTS = ("apo_problem_create", "apo_problem_destroy", "apo_problem_dim", "apo_run", "apo_run_device",
            "apo_run_device_noalloc",
-           "apo_run_batch", "apo_step", "apo_evaluate", "apo_clamp_eval_select", "apo_histogram_u8",
+           "apo_run_batch", "apo_batch_create", "apo_batch_launch", "apo_batch_autotune", "apo_batch_destroy",
+           "apo_step", "apo_evaluate", "apo_clamp_eval_select", "apo_histogram_u8",
            "apo_philox4x32_10", "apo_set_timing_events", "apo_status_string", "apo_last_error")
 
 
@@ -44,6 +45,10 @@ class apo_params(C.Structure):
                 ("seed", C.c_uint32), ("run", C.c_uint32), ("pdr_form", C.c_int)]
 
 
+class apo_batch_options(C.Structure):
+    _fields_ = [("smem_budget", C.c_size_t), ("ctas_per_sm", C.c_int)]
+
+
 _P = C.c_void_p
 _lib.apo_problem_create.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(apo_objective_desc), C.POINTER(_P)]
@@ -57,6 +62,12 @@ _lib.apo_run.argtypes = [_P, C.POINTER(apo_params), _P, C.POINTER(C.c_float), C.
 _lib.apo_run_device.argtypes = [_P, C.POINTER(apo_params), _P, _P, _P, _P]
 _lib.apo_run_device_noalloc.argtypes = [_P, C.POINTER(apo_params), _P, _P, _P, _P]
 _lib.apo_run_batch.argtypes = [C.POINTER(_P), C.POINTER(apo_params), C.c_int, _P, _P, C.c_int, _P, _P, C.c_int]
+_lib.apo_batch_create.argtypes = [C.POINTER(_P), C.POINTER(apo_params), C.c_int, _P, C.c_int, _P, _P, C.c_int,
+                                  C.POINTER(apo_batch_options), C.POINTER(_P)]
+_lib.apo_batch_launch.argtypes = [_P, _P]
+_lib.apo_batch_autotune.argtypes = [_P, _P, C.c_int, C.POINTER(apo_batch_options)]
+_lib.apo_batch_destroy.argtypes = [_P]
+_lib.apo_batch_destroy.restype = None
 _lib.apo_step.argtypes = [_P, C.POINTER(apo_params), C.c_int, _P, _P, _P]
 _lib.apo_evaluate.argtypes = [_P, _P, _P, C.c_int, _P]
 _lib.apo_clamp_eval_select.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
@@ -64,7 +75,8 @@ _lib.apo_histogram_u8.argtypes = [_P, C.c_int64, C.c_int, _P, _P]
 _lib.apo_philox4x32_10.argtypes = [_P, C.c_uint32, C.c_uint32, C.c_int, _P, _P]
 _lib.apo_set_timing_events.argtypes = [_P, _P]
 _lib.apo_set_timing_events.restype = C.c_int
-for _f in ("apo_run", "apo_run_device", "apo_run_device_noalloc", "apo_run_batch", "apo_step", "apo_evaluate", "apo_clamp_eval_select",
+for _f in ("apo_batch_create", "apo_batch_launch", "apo_batch_autotune",
+           "apo_run", "apo_run_device", "apo_run_device_noalloc", "apo_run_batch", "apo_step", "apo_evaluate", "apo_clamp_eval_select",
            "apo_histogram_u8", "apo_philox4x32_10"):
     getattr(_lib, _f).restype = C.c_int
 _lib.apo_status_string.argtypes = [C.c_int]
@@ -204,6 +216,40 @@ def apo_run_batch(probs, params, d_best_x, x_stride, d_best_f, d_curves=None, cu
     prm = (apo_params * n)(*params)
     _check(_lib.apo_run_batch(handles, prm, n, _stream(stream), _dptr(d_best_x), int(x_stride), _dptr(d_best_f),
                               _dptr(d_curves), int(curve_stride)), "apo_run_batch")
+
+
+class Batch:
+    """A prepared batch (apo_batch_create); keeps its problems and outputs alive."""
+
+    def __init__(self, handle, probs, outs):
+        self.handle, self._probs, self._outs = handle, probs, outs
+
+    def launch(self, stream=None):
+        _check(_lib.apo_batch_launch(self.handle, _stream(stream)), "apo_batch_launch")
+
+    def autotune(self, probe_iters=50, stream=None):
+        o = apo_batch_options()
+        _check(_lib.apo_batch_autotune(self.handle, _stream(stream), int(probe_iters), C.byref(o)),
+               "apo_batch_autotune")
+        return {"smem_budget": int(o.smem_budget), "ctas_per_sm": int(o.ctas_per_sm)}
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.apo_batch_destroy(h)
+            self.handle = None
+
+
+def apo_batch_create(probs, params, d_best_x, x_stride, d_best_f, d_curves=None, curve_stride=0,
+                     smem_budget=0, ctas_per_sm=0) -> Batch:
+    n = len(probs)
+    handles = (_P * n)(*[p.handle for p in probs])
+    prm = (apo_params * n)(*params)
+    opt = apo_batch_options(int(smem_budget), int(ctas_per_sm))
+    h = _P()
+    _check(_lib.apo_batch_create(handles, prm, n, _dptr(d_best_x), int(x_stride), _dptr(d_best_f), _dptr(d_curves),
+                                 int(curve_stride), C.byref(opt), C.byref(h)), "apo_batch_create")
+    return Batch(h, list(probs), (d_best_x, d_best_f, d_curves))
 
 
 def apo_step(prob: Problem, params: apo_params, it: int, d_X, d_F, stream=None):

@@ -49,7 +49,7 @@ int next_pow2(int v)
 }
 
 // Largest dynamic shared memory per CTA on sm_100-class parts.
-constexpr size_t kSmemMax = 232448;
+constexpr size_t kSmemMax = 232448 - 2048;  // dynamic part; the kernels use < 1 KB of static shared memory
 // Runs with a larger population go to the cooperative grid launch.
 constexpr int kQueueMaxPs = 1024;
 // Minimum protozoa per CTA in grid mode.
@@ -432,56 +432,104 @@ struct RunSpec {
     void* F_in;
 };
 
-struct Group {
-    bool fit64;
-    int qpl;
-    bool grid;
+// One kernel launch of a prepared set of runs.
+struct LaunchInfo {
+    int first, count;   // runs [first, first + count) of the launch-ordered descriptors
+    bool grid, fit64;
+    int qpl, g, ctas;
     size_t smem;
-    std::vector<int> runs;  // indices into specs
 };
 
-// Plans, allocates and launches a set of runs on one stream.
-apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
+// Everything a set of runs needs on the device, planned and uploaded once;
+// launching it then only clears control words and launches kernels.
+struct Prepared {
+    void* ws = nullptr;         // workspace (descriptors, Dr masks, state, barriers)
+    bool ws_async = false;      // allocated with cudaMallocAsync
+    ApoRun* d_runs = nullptr;   // launch-ordered descriptors
+    int* d_offs = nullptr;
+    int* d_ctrl = nullptr;      // queue counters (one per launch)
+    unsigned char* d_bars = nullptr;  // barrier words, 16 bytes per run
+    int n = 0, n_work = 0, max_ps_pad = 1;
+    std::vector<LaunchInfo> launches;
+    std::vector<RunSpec> order;           // specs in launch order
+    std::vector<size_t> x0_off, f0_off;   // step mode: state copies
+    size_t queue_smem_cap = 0;            // work-queue shared-memory budget used
+};
+
+void release_prepared(Prepared& PR, cudaStream_t st);
+
+// Plans the launches: runs with ps > kQueueMaxPs go to the cooperative grid
+// kernel; the others to the work-queue kernel, resident in shared memory when
+// their layout fits `queue_budget` bytes.  queue_ctas_per_sm limits the
+// persistent work-queue grid (0 = occupancy limit).
+apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, bool async_alloc,
+                        size_t queue_budget, int queue_ctas_per_sm, Prepared* out)
 {
-    const int n = (int)specs.size();
+    Prepared& PR = *out;
+    const int n = (int)specs_in.size();
+    PR.n = n;
     if (n == 0) return APO_OK;
     int dev = 0, sms = 0;
     APO_CUDA(cudaGetDevice(&dev));
     APO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int* status = device_status(dev);
-    if (!status) { set_err("status word allocation failed"); return APO_ERR_OOM; }
+    if (queue_budget == 0 || queue_budget > kSmemMax) queue_budget = kSmemMax;
 
-    std::vector<ApoRun> runs(n);
-    std::vector<char> grid(n, 0);
+    // per-run layout and kernel class
+    struct Cls { bool grid, fit64; int qpl; };
     std::vector<SmemPlan> plans(n);
+    std::vector<Cls> cls(n);
     for (int k = 0; k < n; ++k) {
-        const RunSpec& s = specs[k];
+        const RunSpec& s = specs_in[k];
         const int ps = s.prm.ps;
-        const SmemPlan res = choose_plan(s.P, ps, true, false, kSmemMax);
-        const SmemPlan nres = choose_plan(s.P, ps, false, false, kSmemMax);
-        if (ps > kQueueMaxPs) {
-            grid[k] = 1;
-            const SmemPlan gp = choose_plan(s.P, ps, false, true, kSmemMax);
-            plans[k] = gp;
-            if (gp.total > kSmemMax) { set_err("population %d needs too much shared memory", ps); return APO_ERR_UNSUPPORTED; }
-            if (nres.total > kSmemMax) { set_err("population %d needs too much shared memory", ps); return APO_ERR_UNSUPPORTED; }
-        } else if (res.total <= kSmemMax) {
-            plans[k] = res;
+        const bool f64 = s.P->kind == APO_OBJ_OTSU;
+        cls[k] = {ps > kQueueMaxPs, f64, f64 ? 1 : qpl_of(s.P)};
+        if (cls[k].grid) {
+            plans[k] = choose_plan(s.P, ps, false, true, kSmemMax);
         } else {
-            plans[k] = nres;
-            if (nres.total > kSmemMax) { set_err("problem needs too much shared memory"); return APO_ERR_UNSUPPORTED; }
+            plans[k] = choose_plan(s.P, ps, true, false, queue_budget);
+            if (plans[k].total > queue_budget) plans[k] = choose_plan(s.P, ps, false, false, queue_budget);
+        }
+        if (plans[k].total > kSmemMax) { set_err("problem needs too much shared memory (ps %d)", ps); return APO_ERR_UNSUPPORTED; }
+    }
+    // launch groups: one per kernel class; work-queue runs longest first
+    std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+    for (int k = 0; k < n; ++k) groups[std::make_tuple((int)cls[k].grid, (int)cls[k].fit64, cls[k].qpl)].push_back(k);
+    std::vector<int> order;
+    for (auto& kv : groups) {
+        std::vector<int>& v = kv.second;
+        const Cls c = cls[v[0]];
+        size_t smem = 0;
+        for (int k : v) smem = std::max<size_t>(smem, plans[k].total);
+        if (!c.grid) {
+            auto cost = [&](int k) {
+                const double D = specs_in[k].P->D;
+                return (double)specs_in[k].prm.ps * (D * D + 40.0 * D) * (specs_in[k].t_end - specs_in[k].t_begin + 1);
+            };
+            std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return cost(a) > cost(b); });
+            int cap = run_kernel_capacity(c.fit64, c.qpl, smem, false);
+            if (cap <= 0) { set_err("work-queue kernel cannot be resident with %zu B of shared memory", smem); return APO_ERR_UNSUPPORTED; }
+            if (queue_ctas_per_sm > 0) cap = std::min(cap, queue_ctas_per_sm * sms);
+            PR.launches.push_back({(int)order.size(), (int)v.size(), false, c.fit64, c.qpl, 1, std::min(cap, (int)v.size()), smem});
+            order.insert(order.end(), v.begin(), v.end());
+            PR.queue_smem_cap = std::max(PR.queue_smem_cap, smem);
+            continue;
+        }
+        const int cap = run_kernel_capacity(c.fit64, c.qpl, smem, true);
+        if (cap <= 0) { set_err("grid kernel cannot be resident with %zu B of shared memory", smem); return APO_ERR_UNSUPPORTED; }
+        for (size_t i = 0; i < v.size(); i += (size_t)cap) {
+            const int cnt = (int)std::min(v.size() - i, (size_t)cap);
+            int g = std::min(kMaxGridCtas, cap / cnt);
+            for (int j = 0; j < cnt; ++j) {
+                const int want = (specs_in[v[i + j]].prm.ps + kGridMinRows - 1) / kGridMinRows;
+                g = std::max(1, std::min(g, want));
+            }
+            PR.launches.push_back({(int)order.size(), cnt, true, c.fit64, c.qpl, g, cnt * g, smem});
+            order.insert(order.end(), v.begin() + i, v.begin() + i + cnt);
         }
     }
-    // group by kernel instantiation and mode
-    std::map<std::tuple<int, int, int>, Group> groups;
-    for (int k = 0; k < n; ++k) {
-        const bool f64 = specs[k].P->kind == APO_OBJ_OTSU;
-        const int q = f64 ? 1 : qpl_of(specs[k].P);
-        Group& gr = groups[std::make_tuple((int)f64, q, (int)grid[k])];
-        gr.fit64 = f64; gr.qpl = q; gr.grid = grid[k] != 0;
-        gr.runs.push_back(k);
-        gr.smem = std::max<size_t>(gr.smem, plans[k].total);
-    }
+    PR.order.resize(n);
+    for (int i = 0; i < n; ++i) PR.order[i] = specs_in[order[i]];
+    const std::vector<RunSpec>& specs = PR.order;
 
     // workspace layout
     size_t off = 0;
@@ -493,148 +541,150 @@ apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
     };
     const size_t off_runs = take(sizeof(ApoRun) * n);
     const size_t off_offs = take(sizeof(int) * (n + 1));
-    const size_t off_ctrl = take(sizeof(int) * 64);
-    std::vector<size_t> off_dr(n), off_x0(n), off_x1(n), off_f0(n), off_f1(n), off_bar(n), off_pg(n), off_kg(n);
-    int n_work = 0;
+    const size_t off_ctrl = take(sizeof(int) * std::max<size_t>(PR.launches.size(), 1));
+    const size_t off_bars = take(16 * (size_t)n);
+    std::vector<size_t> off_dr(n), off_x0(n), off_x1(n), off_f0(n), off_f1(n), off_pg(n), off_kg(n);
     std::vector<int> offs(n + 1, 0);
-    int max_ps_pad = 1;
-    for (int k = 0; k < n; ++k) {
-        const RunSpec& s = specs[k];
+    for (int i = 0; i < n; ++i) {
+        const RunSpec& s = specs[i];
+        const int k = order[i];
         const int ps = s.prm.ps, Dp = s.P->Dp;
         const size_t fsz = s.P->kind == APO_OBJ_OTSU ? 8 : 4;
         const int W = (ps + 31) / 32;
-        off_dr[k] = take(sizeof(uint32_t) * W * (size_t)(s.t_end + 1));
+        off_dr[i] = take(sizeof(uint32_t) * W * (size_t)(s.t_end + 1));
         const bool need_global = !plans[k].resident || (s.flags & kFlagStepOut);
-        off_pg[k] = grid[k] ? take((size_t)ps * 4) : 0;
-        off_kg[k] = grid[k] ? take((size_t)ps * (s.P->kind == APO_OBJ_OTSU ? 16 : 8)) : 0;
-        off_x0[k] = need_global ? take((size_t)ps * Dp * 4) : 0;
-        off_x1[k] = need_global ? take((size_t)ps * Dp * 4) : 0;
-        off_f0[k] = need_global ? take(ps * fsz) : 0;
-        off_f1[k] = need_global ? take(ps * fsz) : 0;
-        off_bar[k] = take(16);
-        offs[k] = n_work;
-        n_work += s.t_end - s.t_begin + 1;
-        max_ps_pad = std::max(max_ps_pad, next_pow2(ps));
+        off_x0[i] = need_global ? take((size_t)ps * Dp * 4) : 0;
+        off_x1[i] = need_global ? take((size_t)ps * Dp * 4) : 0;
+        off_f0[i] = need_global ? take(ps * fsz) : 0;
+        off_f1[i] = need_global ? take(ps * fsz) : 0;
+        off_pg[i] = cls[k].grid ? take((size_t)ps * 4) : 0;
+        off_kg[i] = cls[k].grid ? take((size_t)ps * (fsz == 8 ? 16 : 8)) : 0;
+        offs[i] = PR.n_work;
+        PR.n_work += s.t_end - s.t_begin + 1;
+        PR.max_ps_pad = std::max(PR.max_ps_pad, next_pow2(ps));
     }
-    offs[n] = n_work;
-    void* ws = nullptr;
-    APO_CUDA(cudaMallocAsync(&ws, std::max<size_t>(off, 256), st));
-    unsigned char* base = static_cast<unsigned char*>(ws);
-    auto fail = [&](apo_status s) {
-        cudaFreeAsync(ws, st);
-        return s;
-    };
+    offs[n] = PR.n_work;
+    if (async_alloc) {
+        APO_CUDA(cudaMallocAsync(&PR.ws, std::max<size_t>(off, 256), st));
+    } else {
+        APO_CUDA(cudaMalloc(&PR.ws, std::max<size_t>(off, 256)));
+    }
+    PR.ws_async = async_alloc;
+    unsigned char* base = static_cast<unsigned char*>(PR.ws);
+    PR.d_runs = reinterpret_cast<ApoRun*>(base + off_runs);
+    PR.d_offs = reinterpret_cast<int*>(base + off_offs);
+    PR.d_ctrl = reinterpret_cast<int*>(base + off_ctrl);
+    PR.d_bars = base + off_bars;
 
-    for (int k = 0; k < n; ++k) {
-        const RunSpec& s = specs[k];
-        ApoRun& R = runs[k];
+    std::vector<ApoRun> runs(n);
+    std::vector<int> g_of(n, 1);
+    for (const LaunchInfo& L : PR.launches)
+        for (int i = L.first; i < L.first + L.count; ++i) g_of[i] = L.g;
+    for (int i = 0; i < n; ++i) {
+        const RunSpec& s = specs[i];
+        const int k = order[i];
+        ApoRun& R = runs[i];
         std::memset(&R, 0, sizeof(R));
         R.prob = s.P->dev;
         R.plan = plans[k];
         R.ps = s.prm.ps; R.np = s.prm.np; R.T = s.prm.max_iter; R.pdr_form = s.prm.pdr_form;
         R.pf_max = s.prm.pf_max; R.seed = s.prm.seed; R.run = s.prm.run;
         R.t_begin = s.t_begin; R.t_end = s.t_end; R.flags = s.flags;
-        R.g = 1;
+        R.g = g_of[i];
         const uint32_t* thr_dr = nullptr;
         const uint32_t* thr_ah = nullptr;
         const float *fsc = nullptr, *nsc = nullptr;
         apo_status rc = get_thr_dr(R.ps, R.pdr_form, dev, &thr_dr);
         if (rc == APO_OK) rc = get_sched(R.T, dev, &thr_ah, &fsc, &nsc);
-        if (rc != APO_OK) return fail(rc);
+        if (rc != APO_OK) { release_prepared(PR, st); return rc; }
         R.thr_dr = thr_dr; R.thr_ah = thr_ah; R.fsc = fsc; R.nsc = nsc;
-        R.drmask = reinterpret_cast<const uint32_t*>(base + off_dr[k]);
-        if (off_x0[k] || off_x1[k]) {
-            R.X[0] = reinterpret_cast<float*>(base + off_x0[k]);
-            R.X[1] = reinterpret_cast<float*>(base + off_x1[k]);
-            R.F[0] = base + off_f0[k];
-            R.F[1] = base + off_f1[k];
+        R.drmask = reinterpret_cast<const uint32_t*>(base + off_dr[i]);
+        if (off_x0[i] || off_x1[i]) {
+            R.X[0] = reinterpret_cast<float*>(base + off_x0[i]);
+            R.X[1] = reinterpret_cast<float*>(base + off_x1[i]);
+            R.F[0] = base + off_f0[i];
+            R.F[1] = base + off_f1[i];
         }
         R.X_out = s.X_in;
         R.F_out = s.F_in;
         R.best_x = s.best_x; R.best_f = s.best_f; R.curve = s.curve;
-        R.bar = reinterpret_cast<unsigned*>(base + off_bar[k]);
-        if (grid[k]) {
-            R.perm_g = reinterpret_cast<uint32_t*>(base + off_pg[k]);
-            R.keys_g = base + off_kg[k];
+        R.bar = reinterpret_cast<unsigned*>(PR.d_bars + 16 * (size_t)i);
+        if (cls[k].grid) {
+            R.perm_g = reinterpret_cast<uint32_t*>(base + off_pg[i]);
+            R.keys_g = base + off_kg[i];
         }
     }
-    // grid group sizes: g CTAs per run, all co-resident
-    std::vector<std::pair<Group*, std::vector<int>>> launches;  // (group, run subset)
-    for (auto& kv : groups) {
-        Group& gr = kv.second;
-        if (!gr.grid) {
-            launches.emplace_back(&gr, gr.runs);
-            continue;
-        }
-        const int cap = run_kernel_capacity(gr.fit64, gr.qpl, gr.smem, true);
-        if (cap <= 0) { set_err("grid kernel cannot be resident with %zu B of shared memory", gr.smem); return fail(APO_ERR_UNSUPPORTED); }
-        // split into launches of at most `cap` runs (one CTA each at least)
-        for (size_t i = 0; i < gr.runs.size(); i += (size_t)cap) {
-            std::vector<int> sub(gr.runs.begin() + i, gr.runs.begin() + std::min(gr.runs.size(), i + (size_t)cap));
-            const int per = std::min(kMaxGridCtas, cap / (int)sub.size());
-            for (int k : sub) {
-                const int want = (specs[k].prm.ps + kGridMinRows - 1) / kGridMinRows;
-                runs[k].g = std::max(1, std::min(per, want));
-            }
-            // one g per launch: the smallest over the subset
-            int g = per;
-            for (int k : sub) g = std::min(g, runs[k].g);
-            for (int k : sub) runs[k].g = g;
-            launches.emplace_back(&gr, sub);
-        }
+    PR.x0_off = off_x0;
+    PR.f0_off = off_f0;
+    cudaError_t e;
+    if (async_alloc) {
+        e = cudaMemcpyAsync(PR.d_runs, runs.data(), sizeof(ApoRun) * n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(PR.d_offs, offs.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st);
+    } else {
+        e = cudaMemcpy(PR.d_runs, runs.data(), sizeof(ApoRun) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(PR.d_offs, offs.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
     }
-
-    APO_CUDA(cudaMemcpyAsync(base + off_runs, runs.data(), sizeof(ApoRun) * n, cudaMemcpyHostToDevice, st));
-    APO_CUDA(cudaMemcpyAsync(base + off_offs, offs.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
-    APO_CUDA(cudaMemsetAsync(base + off_ctrl, 0, sizeof(int) * 64, st));
-    for (int k = 0; k < n; ++k) {
-        APO_CUDA(cudaMemsetAsync(base + off_bar[k], 0, 16, st));
-        const RunSpec& s = specs[k];
-        if (s.flags & kFlagStepOut) {
-            const size_t fsz = s.P->kind == APO_OBJ_OTSU ? 8 : 4;
-            APO_CUDA(cudaMemcpy2DAsync(base + off_x0[k], (size_t)s.P->Dp * 4, s.X_in, (size_t)s.P->D * 4,
-                                       (size_t)s.P->D * 4, s.prm.ps, cudaMemcpyDeviceToDevice, st));
-            APO_CUDA(cudaMemcpyAsync(base + off_f0[k], s.F_in, s.prm.ps * fsz, cudaMemcpyDeviceToDevice, st));
-        }
+    if (e != cudaSuccess) {
+        set_err("descriptor upload failed: %s", cudaGetErrorString(e));
+        release_prepared(PR, st);
+        return APO_ERR_CUDA;
     }
-    const ApoRun* d_runs = reinterpret_cast<const ApoRun*>(base + off_runs);
-    cudaError_t e = launch_dr(d_runs, reinterpret_cast<const int*>(base + off_offs), n, n_work, max_ps_pad, st);
-    if (e != cudaSuccess) { set_err("Dr selection launch failed: %s", cudaGetErrorString(e)); return fail(APO_ERR_CUDA); }
-
-    // The run kernels index runs through a per-launch table: lay the runs of
-    // each launch out contiguously in a second copy of the descriptors.
-    size_t nl = launches.size();
-    std::vector<ApoRun> ordered;
-    std::vector<int> first(nl, 0);
-    for (size_t l = 0; l < nl; ++l) {
-        first[l] = (int)ordered.size();
-        for (int k : launches[l].second) ordered.push_back(runs[k]);
-    }
-    ApoRun* d_ordered = nullptr;
-    APO_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_ordered), sizeof(ApoRun) * ordered.size(), st));
-    if (nl > 64) { set_err("too many launch groups"); return fail(APO_ERR_INTERNAL); }
-    e = cudaMemcpyAsync(d_ordered, ordered.data(), sizeof(ApoRun) * ordered.size(), cudaMemcpyHostToDevice, st);
-    const bool timed = g_ev_before && g_ev_after && !(specs[0].flags & kFlagStepOut);
-    if (timed && e == cudaSuccess) e = cudaEventRecord(g_ev_before, st);
-    for (size_t l = 0; l < nl && e == cudaSuccess; ++l) {
-        Group& gr = *launches[l].first;
-        const int cnt = (int)launches[l].second.size();
-        int* queue = reinterpret_cast<int*>(base + off_ctrl) + (int)l;
-        if (gr.grid) {
-            e = launch_run(d_ordered + first[l], cnt, ordered[first[l]].g, 0, queue, status, gr.smem, gr.fit64,
-                           gr.qpl, st);
-        } else {
-            const int cap = run_kernel_capacity(gr.fit64, gr.qpl, gr.smem, false);
-            if (cap <= 0) { e = cudaErrorInvalidConfiguration; break; }
-            e = launch_run(d_ordered + first[l], cnt, 0, std::min(cap, cnt), queue, status, gr.smem, gr.fit64,
-                           gr.qpl, st);
-        }
-    }
-    if (timed && e == cudaSuccess) e = cudaEventRecord(g_ev_after, st);
-    cudaFreeAsync(d_ordered, st);
-    if (e != cudaSuccess) { set_err("run launch failed: %s", cudaGetErrorString(e)); return fail(APO_ERR_CUDA); }
-    APO_CUDA(cudaFreeAsync(ws, st));
     return APO_OK;
+}
+
+// Clears the control words and launches the Dr_index and iteration-loop
+// kernels of a prepared set of runs on `st` (no allocation, no host copy:
+// capturable in a CUDA graph when no run is in step mode).
+apo_status launch_prepared(const Prepared& PR, cudaStream_t st)
+{
+    if (PR.n == 0) return APO_OK;
+    int dev = 0;
+    APO_CUDA(cudaGetDevice(&dev));
+    int* status = device_status(dev);
+    if (!status) { set_err("status word allocation failed"); return APO_ERR_OOM; }
+    unsigned char* base = static_cast<unsigned char*>(PR.ws);
+    APO_CUDA(cudaMemsetAsync(PR.d_ctrl, 0, sizeof(int) * std::max<size_t>(PR.launches.size(), 1), st));
+    APO_CUDA(cudaMemsetAsync(PR.d_bars, 0, 16 * (size_t)PR.n, st));
+    for (int i = 0; i < PR.n; ++i) {
+        const RunSpec& s = PR.order[i];
+        if (!(s.flags & kFlagStepOut)) continue;
+        const size_t fsz = s.P->kind == APO_OBJ_OTSU ? 8 : 4;
+        APO_CUDA(cudaMemcpy2DAsync(base + PR.x0_off[i], (size_t)s.P->Dp * 4, s.X_in, (size_t)s.P->D * 4,
+                                   (size_t)s.P->D * 4, s.prm.ps, cudaMemcpyDeviceToDevice, st));
+        APO_CUDA(cudaMemcpyAsync(base + PR.f0_off[i], s.F_in, s.prm.ps * fsz, cudaMemcpyDeviceToDevice, st));
+    }
+    cudaError_t e = launch_dr(PR.d_runs, PR.d_offs, PR.n, PR.n_work, PR.max_ps_pad, st);
+    if (e != cudaSuccess) { set_err("Dr selection launch failed: %s", cudaGetErrorString(e)); return APO_ERR_CUDA; }
+    const bool timed = g_ev_before && g_ev_after && !(PR.order[0].flags & kFlagStepOut);
+    if (timed) APO_CUDA(cudaEventRecord(g_ev_before, st));
+    for (size_t l = 0; l < PR.launches.size() && e == cudaSuccess; ++l) {
+        const LaunchInfo& L = PR.launches[l];
+        e = launch_run(PR.d_runs + L.first, L.count, L.grid ? L.g : 0, L.ctas, PR.d_ctrl + l, status, L.smem,
+                       L.fit64, L.qpl, st);
+    }
+    if (e != cudaSuccess) { set_err("run launch failed: %s", cudaGetErrorString(e)); return APO_ERR_CUDA; }
+    if (timed) APO_CUDA(cudaEventRecord(g_ev_after, st));
+    return APO_OK;
+}
+
+void release_prepared(Prepared& PR, cudaStream_t st)
+{
+    if (PR.ws) {
+        if (PR.ws_async) cudaFreeAsync(PR.ws, st);
+        else cudaFree(PR.ws);
+    }
+    PR.ws = nullptr;
+}
+
+// Plans, allocates (stream-ordered) and launches a set of runs on one stream.
+apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
+{
+    Prepared PR;
+    apo_status rc = prepare_runs(specs, st, true, 0, 0, &PR);
+    if (rc != APO_OK) return rc;
+    rc = launch_prepared(PR, st);
+    release_prepared(PR, st);
+    return rc;
 }
 
 apo_status read_device_status(int dev)
@@ -699,6 +749,7 @@ extern "C" apo_status apo_run_batch(const apo_problem* const* probs, const apo_p
                                     void* stream, float* d_best_x, int x_stride, double* d_best_f,
                                     float* d_curves, int curve_stride)
 {
+    // (planning as in apo_batch_create, with a stream-ordered workspace)
     if (n_runs < 0 || (n_runs > 0 && (!probs || !params || !d_best_x || !d_best_f))) {
         set_err("invalid batch arguments");
         return APO_ERR_INVALID_ARG;
@@ -719,6 +770,124 @@ extern "C" apo_status apo_run_batch(const apo_problem* const* probs, const apo_p
         s.X_in = nullptr; s.F_in = nullptr;
     }
     return launch_runs(specs, static_cast<cudaStream_t>(stream));
+}
+
+struct apo_batch {
+    std::vector<RunSpec> specs;
+    apo_batch_options opt;
+    Prepared prep;
+};
+
+namespace {
+
+apo_status batch_specs(const apo_problem* const* probs, const apo_params* params, int n_runs, float* d_best_x,
+                       int x_stride, double* d_best_f, float* d_curves, int curve_stride,
+                       std::vector<RunSpec>& specs)
+{
+    if (n_runs < 0 || (n_runs > 0 && (!probs || !params || !d_best_x || !d_best_f))) {
+        set_err("invalid batch arguments");
+        return APO_ERR_INVALID_ARG;
+    }
+    specs.resize(n_runs);
+    for (int k = 0; k < n_runs; ++k) {
+        apo_status rc = check_params(probs[k], &params[k]);
+        if (rc != APO_OK) return rc;
+        if (x_stride < probs[k]->D || (d_curves && curve_stride < params[k].max_iter + 1)) {
+            set_err("x_stride / curve_stride too small for run %d", k);
+            return APO_ERR_INVALID_ARG;
+        }
+        RunSpec& s = specs[k];
+        s.P = probs[k]; s.prm = params[k]; s.t_begin = 1; s.t_end = params[k].max_iter; s.flags = kFlagInit;
+        s.best_x = d_best_x + (size_t)k * x_stride;
+        s.best_f = d_best_f + k;
+        s.curve = d_curves ? d_curves + (size_t)k * curve_stride : nullptr;
+        s.X_in = nullptr; s.F_in = nullptr;
+    }
+    return APO_OK;
+}
+
+}  // namespace
+
+extern "C" apo_status apo_batch_create(const apo_problem* const* probs, const apo_params* params, int n_runs,
+                                       float* d_best_x, int x_stride, double* d_best_f, float* d_curves,
+                                       int curve_stride, const apo_batch_options* opt, apo_batch** out)
+{
+    if (!out) { set_err("out is NULL"); return APO_ERR_INVALID_ARG; }
+    *out = nullptr;
+    apo_batch* B = new apo_batch();
+    apo_status rc = batch_specs(probs, params, n_runs, d_best_x, x_stride, d_best_f, d_curves, curve_stride, B->specs);
+    if (rc != APO_OK) { delete B; return rc; }
+    B->opt.smem_budget = opt ? opt->smem_budget : 0;
+    B->opt.ctas_per_sm = opt ? opt->ctas_per_sm : 0;
+    rc = prepare_runs(B->specs, 0, false, B->opt.smem_budget, B->opt.ctas_per_sm, &B->prep);
+    if (rc != APO_OK) { delete B; return rc; }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!device_status(dev)) { release_prepared(B->prep, 0); delete B; set_err("status word allocation failed"); return APO_ERR_OOM; }
+    *out = B;
+    return APO_OK;
+}
+
+extern "C" apo_status apo_batch_launch(apo_batch* B, void* stream)
+{
+    if (!B) { set_err("batch is NULL"); return APO_ERR_INVALID_ARG; }
+    return launch_prepared(B->prep, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" void apo_batch_destroy(apo_batch* B)
+{
+    if (!B) return;
+    cudaDeviceSynchronize();
+    release_prepared(B->prep, 0);
+    delete B;
+}
+
+extern "C" apo_status apo_batch_autotune(apo_batch* B, void* stream, int probe_iters, apo_batch_options* chosen)
+{
+    if (!B || probe_iters < 1) { set_err("invalid autotune arguments"); return APO_ERR_INVALID_ARG; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<RunSpec> probe = B->specs;
+    for (RunSpec& s : probe) s.t_end = std::min(s.t_end, probe_iters);
+    const size_t budgets[4] = {kSmemMax, 113 * 1024, 75 * 1024, 56 * 1024};
+    cudaEvent_t e0, e1;
+    APO_CUDA(cudaEventCreate(&e0));
+    APO_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    apo_batch_options best = B->opt;
+    for (size_t c = 0; c < 4; ++c) {
+        Prepared PR;
+        if (prepare_runs(probe, st, false, budgets[c], 0, &PR) != APO_OK) continue;
+        float ms = 1e30f;
+        bool ok = launch_prepared(PR, st) == APO_OK;   // warm-up
+        for (int rep = 0; rep < 2 && ok; ++rep) {
+            cudaEventRecord(e0, st);
+            ok = launch_prepared(PR, st) == APO_OK;
+            cudaEventRecord(e1, st);
+            if (ok && cudaEventSynchronize(e1) == cudaSuccess) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                ms = std::min(ms, t);
+            }
+        }
+        cudaStreamSynchronize(st);
+        release_prepared(PR, st);
+        if (ok && ms < best_ms) {
+            best_ms = ms;
+            best.smem_budget = budgets[c];
+            best.ctas_per_sm = 0;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms >= 1e30f) { set_err("no autotune candidate ran"); return APO_ERR_INTERNAL; }
+    cudaStreamSynchronize(st);
+    release_prepared(B->prep, st);
+    B->prep = Prepared();
+    B->opt = best;
+    apo_status rc = prepare_runs(B->specs, st, false, best.smem_budget, best.ctas_per_sm, &B->prep);
+    if (rc != APO_OK) return rc;
+    if (chosen) *chosen = best;
+    return APO_OK;
 }
 
 extern "C" apo_status apo_step(const apo_problem* P, const apo_params* p, int iter, void* stream, float* d_X,

@@ -34,7 +34,7 @@ static __device__ __align__(256) unsigned char apo_noalloc_scratch[8u << 20];
 namespace {
 
 constexpr size_t kScratchBytes = 8u << 20;
-constexpr size_t kSmemMaxNA = 232448;
+constexpr size_t kSmemMaxNA = 232448 - 2048;
 constexpr int kQueueMaxPsNA = 1024;
 constexpr int kGridMinRowsNA = 8;
 constexpr int kMaxDevices = 64;

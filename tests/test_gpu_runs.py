@@ -179,3 +179,38 @@ def test_lockstep_every_iteration_of_a_run(apo, orc, seed):
         assert close(Xg, want_X).all(), t
         assert close(Fg, want_F).all(), t
     assert flips <= 0.01 * ps * T
+
+
+def test_prepared_batch_autotune_and_graph_replay(apo):
+    """apo_batch_create / autotune / launch and a CUDA-graph replay of the launch
+    reproduce apo_run_batch bit for bit on a mixed batch (resident and
+    global-memory work-queue runs)."""
+    import torch
+    runs = inputs.batched_runs(n_runs=24, seed=3)
+    T = 40
+    probs = [apo.problem_from_spec(s) for s, _ in runs]
+    prms = [apo.apo_params_make(ps, 1, 0.1, T, 5, k) for k, (_, ps) in enumerate(runs)]
+    n = len(runs)
+    ref_x = torch.zeros((n, 50), device="cuda")
+    ref_f = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ref_c = torch.zeros((n, T + 1), device="cuda")
+    apo.apo_run_batch(probs, prms, ref_x, 50, ref_f, ref_c, T + 1)
+    torch.cuda.synchronize()
+    bx = torch.zeros_like(ref_x)
+    bf = torch.zeros_like(ref_f)
+    bc = torch.zeros_like(ref_c)
+    b = apo.apo_batch_create(probs, prms, bx, 50, bf, bc, T + 1)
+    chosen = b.autotune(probe_iters=10)
+    assert chosen["smem_budget"] > 0
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.launch(s)
+    s.synchronize()
+    assert torch.equal(bf, ref_f) and torch.equal(bc, ref_c) and torch.equal(bx, ref_x)
+    bf.zero_(); bc.zero_(); bx.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.launch(s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(bf, ref_f) and torch.equal(bc, ref_c) and torch.equal(bx, ref_x)
