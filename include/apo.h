@@ -208,6 +208,31 @@ apo_status apo_clamp_eval_select(const apo_problem* prob, void* stream, int n, f
 apo_status apo_histogram_u8(const uint8_t* d_pixels, int64_t n_pixels_per_image, int n_images,
                             int32_t* d_hist, void* stream);
 
+/* Surrogate network of the surrogate-assisted form: an MLP D -> 256 -> 256 -> 1
+ * with ReLU, bfloat16 weights and activations, float32 accumulation on the
+ * tensor cores, float32 master weights and Adam (lr, beta1 0.9, beta2 0.999,
+ * eps 1e-8) on mean squared error.  Parameters are row-major: W1 [D][256],
+ * b1 [256], W2 [256][256], b2 [256], w3 [256], b3.  The paper has no
+ * counterpart: the surrogate is an added form of the method. */
+typedef struct apo_mlp apo_mlp;
+
+apo_status apo_mlp_create(int D, uint32_t seed, apo_mlp** out);   /* He-uniform init */
+void apo_mlp_destroy(apo_mlp* mlp);
+apo_status apo_mlp_set_params(apo_mlp* mlp, const float* W1, const float* b1, const float* W2, const float* b2,
+                              const float* w3, float b3);   /* host arrays; synchronous */
+apo_status apo_mlp_get_params(const apo_mlp* mlp, float* W1, float* b1, float* W2, float* b2, float* w3,
+                              float* b3);                   /* host outputs; synchronous */
+/* y [n] = f(X [n][D]) for float32 inputs on the device (rounded to bf16). Stream-ordered. */
+apo_status apo_mlp_forward(apo_mlp* mlp, const float* d_X, int n, float* d_y, void* stream);
+/* Test hook: loss and gradients of mean((f(X) - t)^2) over n <= 2048 rows,
+ * written to host arrays (any may be NULL).  Synchronous. */
+apo_status apo_mlp_gradients(apo_mlp* mlp, const float* d_X, const float* d_t, int n, float* gW1, float* gb1,
+                             float* gW2, float* gb2, float* gw3, float* gb3, float* loss);
+/* `steps` Adam steps on batches of `batch` rows drawn uniformly (Philox,
+ * seeded) from the n rows of (d_X, d_t).  Stream-ordered. */
+apo_status apo_mlp_train(apo_mlp* mlp, const float* d_X, const float* d_t, int n, int steps, int batch, float lr,
+                         uint32_t seed, void* stream);
+
 /* Test hook: the device Philox4x32-10 on n counters d_ctr [n*4] with key
  * (key0, key1) into d_out [n*4].  Stream-ordered. */
 apo_status apo_philox4x32_10(const uint32_t* d_ctr, uint32_t key0, uint32_t key1, int n,

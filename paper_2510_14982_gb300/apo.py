@@ -30,6 +30,8 @@ EXPORTS = ("apo_problem_create", "apo_problem_destroy", "apo_problem_dim", "apo_
            "apo_run_device_noalloc",
            "apo_run_batch", "apo_batch_create", "apo_batch_launch", "apo_batch_autotune", "apo_batch_destroy",
            "apo_step", "apo_evaluate", "apo_clamp_eval_select", "apo_histogram_u8",
+           "apo_mlp_create", "apo_mlp_destroy", "apo_mlp_set_params", "apo_mlp_get_params", "apo_mlp_forward",
+           "apo_mlp_gradients", "apo_mlp_train",
            "apo_philox4x32_10", "apo_set_timing_events", "apo_status_string", "apo_last_error")
 
 
@@ -73,6 +75,18 @@ _lib.apo_evaluate.argtypes = [_P, _P, _P, C.c_int, _P]
 _lib.apo_clamp_eval_select.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
 _lib.apo_histogram_u8.argtypes = [_P, C.c_int64, C.c_int, _P, _P]
 _lib.apo_philox4x32_10.argtypes = [_P, C.c_uint32, C.c_uint32, C.c_int, _P, _P]
+_FP = C.POINTER(C.c_float)
+_lib.apo_mlp_create.argtypes = [C.c_int, C.c_uint32, C.POINTER(_P)]
+_lib.apo_mlp_destroy.argtypes = [_P]
+_lib.apo_mlp_destroy.restype = None
+_lib.apo_mlp_set_params.argtypes = [_P, _FP, _FP, _FP, _FP, _FP, C.c_float]
+_lib.apo_mlp_get_params.argtypes = [_P, _FP, _FP, _FP, _FP, _FP, _FP]
+_lib.apo_mlp_forward.argtypes = [_P, _P, C.c_int, _P, _P]
+_lib.apo_mlp_gradients.argtypes = [_P, _P, _P, C.c_int, _FP, _FP, _FP, _FP, _FP, _FP, _FP]
+_lib.apo_mlp_train.argtypes = [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_float, C.c_uint32, _P]
+for _f in ("apo_mlp_create", "apo_mlp_set_params", "apo_mlp_get_params", "apo_mlp_forward", "apo_mlp_gradients",
+           "apo_mlp_train"):
+    getattr(_lib, _f).restype = C.c_int
 _lib.apo_set_timing_events.argtypes = [_P, _P]
 _lib.apo_set_timing_events.restype = C.c_int
 for _f in ("apo_batch_create", "apo_batch_launch", "apo_batch_autotune",
@@ -284,6 +298,52 @@ def apo_set_timing_events(before, after):
     b = None if before is None else C.c_void_p(before.cuda_event)
     a = None if after is None else C.c_void_p(after.cuda_event)
     _check(_lib.apo_set_timing_events(b, a), "apo_set_timing_events")
+
+
+class Mlp:
+    """Surrogate network handle (apo_mlp_create / apo_mlp_destroy)."""
+
+    H = 256
+
+    def __init__(self, D, seed=0):
+        self.D = int(D)
+        h = _P()
+        _check(_lib.apo_mlp_create(self.D, int(seed) & 0xFFFFFFFF, C.byref(h)), "apo_mlp_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.apo_mlp_destroy(h)
+            self.handle = None
+
+    def set_params(self, W1, b1, W2, b2, w3, b3):
+        a = [np.ascontiguousarray(x, np.float32) for x in (W1, b1, W2, b2, w3)]
+        _check(_lib.apo_mlp_set_params(self.handle, *[_np_ptr(x, C.c_float) for x in a], float(b3)),
+               "apo_mlp_set_params")
+
+    def get_params(self):
+        H = self.H
+        out = [np.empty((self.D, H), np.float32), np.empty(H, np.float32), np.empty((H, H), np.float32),
+               np.empty(H, np.float32), np.empty(H, np.float32), np.empty(1, np.float32)]
+        _check(_lib.apo_mlp_get_params(self.handle, *[_np_ptr(x, C.c_float) for x in out]), "apo_mlp_get_params")
+        return dict(W1=out[0], b1=out[1], W2=out[2], b2=out[3], w3=out[4], b3=float(out[5][0]))
+
+    def forward(self, d_X, d_y, stream=None):
+        _check(_lib.apo_mlp_forward(self.handle, _dptr(d_X), int(d_X.shape[0]), _dptr(d_y), _stream(stream)),
+               "apo_mlp_forward")
+
+    def gradients(self, d_X, d_t):
+        H = self.H
+        g = [np.empty((self.D, H), np.float32), np.empty(H, np.float32), np.empty((H, H), np.float32),
+             np.empty(H, np.float32), np.empty(H, np.float32), np.empty(1, np.float32), np.empty(1, np.float32)]
+        _check(_lib.apo_mlp_gradients(self.handle, _dptr(d_X), _dptr(d_t), int(d_X.shape[0]),
+                                      *[_np_ptr(x, C.c_float) for x in g]), "apo_mlp_gradients")
+        return dict(W1=g[0], b1=g[1], W2=g[2], b2=g[3], w3=g[4], b3=float(g[5][0])), float(g[6][0])
+
+    def train(self, d_X, d_t, steps, batch, lr=1e-3, seed=0, stream=None):
+        _check(_lib.apo_mlp_train(self.handle, _dptr(d_X), _dptr(d_t), int(d_X.shape[0]), int(steps), int(batch),
+                                  float(lr), int(seed) & 0xFFFFFFFF, _stream(stream)), "apo_mlp_train")
 
 
 def raw_lib():
