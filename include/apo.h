@@ -233,6 +233,45 @@ apo_status apo_mlp_gradients(apo_mlp* mlp, const float* d_X, const float* d_t, i
 apo_status apo_mlp_train(apo_mlp* mlp, const float* d_X, const float* d_t, int n, int steps, int batch, float lr,
                          uint32_t seed, void* stream);
 
+/* Surrogate-assisted APO (an added form; the paper has no counterpart).  Each
+ * iteration every protozoon draws k candidates (candidate c >= 1 uses the
+ * Philox slots of candidate 0 offset by c << 8, so k = 1 is the plain method
+ * draw for draw), the network ranks them, and only the best-ranked one is
+ * evaluated exactly and goes through the greedy replacement of Algorithm 1.
+ * Exact evaluations fill a ring-buffer archive of archive_cap rows (inputs
+ * scaled to [-1, 1] by the bounds, targets the standardised
+ * log1p(F - min F)); every retrain_every iterations the network takes
+ * train_steps Adam steps on batches of `batch` archive rows.  Screening
+ * starts after the first retrain and stops, until the next retrain, when the
+ * Spearman rank correlation between predicted and true fitness of the last
+ * screened batch is below min_rank_corr (the plain method is the fallback).
+ * Outputs as in apo_run (host); stats (optional) counts the work.
+ * Synchronous.  ps <= 4096; float objectives only. */
+typedef struct apo_surrogate_params {
+    int k;                /* candidates per protozoon, 1..32            */
+    int retrain_every;    /* iterations between retrains                */
+    int archive_cap;      /* archive rows (>= ps)                       */
+    int train_steps;      /* Adam steps per retrain                     */
+    int batch;            /* training batch rows                        */
+    float lr;             /* Adam learning rate                         */
+    float min_rank_corr;  /* screening threshold on Spearman correlation */
+    uint32_t net_seed;    /* network initialisation and batch sampling  */
+} apo_surrogate_params;
+
+typedef struct apo_surrogate_stats {
+    long long true_evals;   /* exact objective evaluations (incl. initial) */
+    long long screened;     /* candidates generated                        */
+    int retrains;
+    int screening_iters;    /* iterations with k > 1                       */
+    int fallback_iters;     /* plain iterations after the first retrain    */
+    double last_rank_corr;
+    double train_ms;        /* device time spent training                  */
+    double total_ms;        /* device time of the whole run                */
+} apo_surrogate_stats;
+
+apo_status apo_run_surrogate(const apo_problem* prob, const apo_params* params, const apo_surrogate_params* sp,
+                             void* stream, float* best_x, double* best_f, float* curve, apo_surrogate_stats* stats);
+
 /* Test hook: the device Philox4x32-10 on n counters d_ctr [n*4] with key
  * (key0, key1) into d_out [n*4].  Stream-ordered. */
 apo_status apo_philox4x32_10(const uint32_t* d_ctr, uint32_t key0, uint32_t key1, int n,

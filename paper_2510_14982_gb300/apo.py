@@ -32,6 +32,7 @@ EXPORTS = ("apo_problem_create", "apo_problem_destroy", "apo_problem_dim", "apo_
            "apo_step", "apo_evaluate", "apo_clamp_eval_select", "apo_histogram_u8",
            "apo_mlp_create", "apo_mlp_destroy", "apo_mlp_set_params", "apo_mlp_get_params", "apo_mlp_forward",
            "apo_mlp_gradients", "apo_mlp_train",
+           "apo_run_surrogate",
            "apo_philox4x32_10", "apo_set_timing_events", "apo_status_string", "apo_last_error")
 
 
@@ -49,6 +50,17 @@ class apo_params(C.Structure):
 
 class apo_batch_options(C.Structure):
     _fields_ = [("smem_budget", C.c_size_t), ("ctas_per_sm", C.c_int)]
+
+
+class apo_surrogate_params(C.Structure):
+    _fields_ = [("k", C.c_int), ("retrain_every", C.c_int), ("archive_cap", C.c_int), ("train_steps", C.c_int),
+                ("batch", C.c_int), ("lr", C.c_float), ("min_rank_corr", C.c_float), ("net_seed", C.c_uint32)]
+
+
+class apo_surrogate_stats(C.Structure):
+    _fields_ = [("true_evals", C.c_longlong), ("screened", C.c_longlong), ("retrains", C.c_int),
+                ("screening_iters", C.c_int), ("fallback_iters", C.c_int), ("last_rank_corr", C.c_double),
+                ("train_ms", C.c_double), ("total_ms", C.c_double)]
 
 
 _P = C.c_void_p
@@ -87,6 +99,9 @@ _lib.apo_mlp_train.argtypes = [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_float,
 for _f in ("apo_mlp_create", "apo_mlp_set_params", "apo_mlp_get_params", "apo_mlp_forward", "apo_mlp_gradients",
            "apo_mlp_train"):
     getattr(_lib, _f).restype = C.c_int
+_lib.apo_run_surrogate.argtypes = [_P, C.POINTER(apo_params), C.POINTER(apo_surrogate_params), _P, _FP,
+                                   C.POINTER(C.c_double), _FP, C.POINTER(apo_surrogate_stats)]
+_lib.apo_run_surrogate.restype = C.c_int
 _lib.apo_set_timing_events.argtypes = [_P, _P]
 _lib.apo_set_timing_events.restype = C.c_int
 for _f in ("apo_batch_create", "apo_batch_launch", "apo_batch_autotune",
@@ -344,6 +359,25 @@ class Mlp:
     def train(self, d_X, d_t, steps, batch, lr=1e-3, seed=0, stream=None):
         _check(_lib.apo_mlp_train(self.handle, _dptr(d_X), _dptr(d_t), int(d_X.shape[0]), int(steps), int(batch),
                                   float(lr), int(seed) & 0xFFFFFFFF, _stream(stream)), "apo_mlp_train")
+
+
+def surrogate_params(k=8, retrain_every=10, archive_cap=50000, train_steps=100, batch=1024, lr=1e-3,
+                     min_rank_corr=0.3, net_seed=0):
+    return apo_surrogate_params(int(k), int(retrain_every), int(archive_cap), int(train_steps), int(batch), float(lr),
+                                float(min_rank_corr), int(net_seed) & 0xFFFFFFFF)
+
+
+def apo_run_surrogate(prob: Problem, params: apo_params, sp: apo_surrogate_params, stream=None, want_curve=True):
+    """apo_run_surrogate (host outputs, synchronous): (best_x, best_f, curve, stats dict)."""
+    best_x = np.empty(prob.D, np.float32)
+    best_f = C.c_double()
+    curve = np.empty(params.max_iter + 1, np.float32) if want_curve else None
+    st = apo_surrogate_stats()
+    _check(_lib.apo_run_surrogate(prob.handle, C.byref(params), C.byref(sp), _stream(stream),
+                                  _np_ptr(best_x, C.c_float), C.byref(best_f), _np_ptr(curve, C.c_float),
+                                  C.byref(st)), "apo_run_surrogate")
+    stats = {f: getattr(st, f) for f, _ in apo_surrogate_stats._fields_}
+    return best_x, best_f.value, curve, stats
 
 
 def raw_lib():

@@ -78,6 +78,29 @@ extern "C" const char* apo_status_string(apo_status s)
 
 extern "C" const char* apo_last_error(void) { return g_err; }
 
+namespace {
+apo_status get_thr_dr(int ps, int form, int dev, const uint32_t** out);
+apo_status get_sched(int T, int dev, const uint32_t** thr_ah, const float** fsc, const float** nsc);
+int* device_status(int dev);
+}  // namespace
+
+apo_status apo::sched_tables(int ps, int pdr_form, int T, const uint32_t** thr_dr, const uint32_t** thr_ah,
+                      const float** fsc, const float** nsc)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    apo_status rc = get_thr_dr(ps, pdr_form, dev, thr_dr);
+    if (rc == APO_OK) rc = get_sched(T, dev, thr_ah, fsc, nsc);
+    return rc;
+}
+
+int* apo::device_status_word()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return device_status(dev);
+}
+
 void apo::set_last_error(const char* msg) { set_err("%s", msg); }
 
 // ---------------------------------------------------------- problems

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/apo.h"
 #include "apo_device.cuh"
 
 // A problem created by apo_problem_create: device copies of the bounds,
@@ -45,6 +46,14 @@ int run_kernel_capacity(bool fit64, int qpl, size_t smem_bytes, bool grid);
 cudaError_t launch_eval(const ApoRun* d_run, int n, const float* d_X, void* d_F, int select,
                         float* d_Xsel, void* d_Fsel, size_t smem_bytes, bool fit64, int qpl,
                         cudaStream_t st);
+
+// Schedule tables of Eq. 4, 9, 12 and 13 (cached per device; allocated on
+// first use).
+apo_status sched_tables(int ps, int pdr_form, int T, const uint32_t** thr_dr, const uint32_t** thr_ah,
+                                const float** fsc, const float** nsc);
+
+// Process-wide device status word (first device-side error wins).
+int* device_status_word();
 
 // Sets the text that apo_last_error() returns on the calling thread.
 void set_last_error(const char* msg);

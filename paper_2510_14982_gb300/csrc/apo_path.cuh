@@ -1,0 +1,511 @@
+// apo_path.cuh -- per-CTA building blocks of the APO update shared by the
+// fused iteration-loop kernels and the surrogate-assisted form: the shared
+// memory carve-up, constant loading, candidate generation (Eq. 1-13), the
+// rotation GEMM, the objective epilogues and the evaluation of a chunk.
+#pragma once
+
+#include "apo_device.cuh"
+
+namespace apo {
+
+constexpr float kEps = 2.220446049250313e-16f;  // eps of Eq. 7 and Eq. 10 (2^-52)
+
+// ------------------------------------------------------- shared layout
+template <typename FitT>
+struct Smem {
+    float* X[2];
+    FitT* F[2];
+    uint32_t* perm[2];
+    void* keys;
+    float* MT;
+    float *o, *lb, *ub, *ew;
+    float *Xc, *Xo, *Yc, *Zc;
+    FitT* rowF;
+    float *compG, *compA;
+    long long *P0, *P1;
+    int* otsu;
+    void* red;
+    int* seg;
+};
+
+template <typename FitT>
+__device__ __forceinline__ Smem<FitT> carve(unsigned char* base, const SmemPlan& L)
+{
+    Smem<FitT> S;
+    S.X[0] = reinterpret_cast<float*>(base + L.X0);
+    S.X[1] = reinterpret_cast<float*>(base + L.X1);
+    S.F[0] = reinterpret_cast<FitT*>(base + L.F0);
+    S.F[1] = reinterpret_cast<FitT*>(base + L.F1);
+    S.perm[0] = reinterpret_cast<uint32_t*>(base + L.perm0);
+    S.perm[1] = reinterpret_cast<uint32_t*>(base + L.perm1);
+    S.keys = base + L.keys;
+    S.MT = reinterpret_cast<float*>(base + L.MT);
+    S.o = reinterpret_cast<float*>(base + L.o);
+    S.lb = reinterpret_cast<float*>(base + L.lb);
+    S.ub = reinterpret_cast<float*>(base + L.ub);
+    S.ew = reinterpret_cast<float*>(base + L.ew);
+    S.Xc = reinterpret_cast<float*>(base + L.Xc);
+    S.Xo = reinterpret_cast<float*>(base + L.Xo);
+    S.Yc = reinterpret_cast<float*>(base + L.Yc);
+    S.Zc = reinterpret_cast<float*>(base + L.Zc);
+    S.rowF = reinterpret_cast<FitT*>(base + L.rowF);
+    S.compG = reinterpret_cast<float*>(base + L.compG);
+    S.compA = reinterpret_cast<float*>(base + L.compA);
+    S.P0 = reinterpret_cast<long long*>(base + L.P0);
+    S.P1 = reinterpret_cast<long long*>(base + L.P1);
+    S.otsu = reinterpret_cast<int*>(base + L.otsu);
+    S.red = base + L.red;
+    S.seg = reinterpret_cast<int*>(base + L.seg);
+    return S;
+}
+
+// Loads the run's constant vectors (and the rotation of a single-component
+// objective when it fits) into shared memory.
+template <typename FitT>
+__device__ __forceinline__ void load_constants(const ApoRun& R, const Smem<FitT>& S)
+{
+    const DevProblem& P = R.prob;
+    const int Dp = P.Dp;
+    const DevComp& C = P.comp[0];
+    for (int i = threadIdx.x; i < Dp; i += blockDim.x) {
+        S.lb[i] = P.lb[i];
+        S.ub[i] = P.ub[i];
+        S.o[i] = C.o ? C.o[i] : 0.f;
+        S.ew[i] = C.ew ? C.ew[i] : 1.f;
+    }
+    if (R.plan.mt_smem && C.MT) {
+        const float4* src = reinterpret_cast<const float4*>(C.MT);
+        float4* dst = reinterpret_cast<float4*>(S.MT);
+        for (int i = threadIdx.x; i < Dp * P.Np / 4; i += blockDim.x) dst[i] = src[i];
+    }
+    if (P.kind == kOtsu) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+            S.P0[i] = P.P0[i];
+            S.P1[i] = P.P1[i];
+        }
+    }
+}
+
+// ------------------------------------------------------------ evaluation
+// 16-byte shared-memory load through an explicit shared-window address.
+__device__ __forceinline__ float4 lds4(uint32_t addr)
+{
+    float4 v;
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
+
+// Z[rows][Np] = Y[rows][Dp] * MT[Dp][Np] with Y stored transposed (YT[k][row],
+// row stride CH) and both operands zero padded beyond D.  FP32 FMA.  A warp
+// computes an 8-row x 128-column tile, lane L the columns 4L..4L+3 of the 8
+// rows: per k the 8 row values are two broadcast 16-byte loads shared by the
+// whole warp and the columns one 16-byte load per lane.  MT_SHARED selects a
+// rotation held in shared memory (explicit ld.shared) or read through L1.
+template <bool MT_SHARED, int TR>
+__device__ __forceinline__ void tile_gemm_t(const float* __restrict__ YT, const float* __restrict__ MT,
+                                            float* __restrict__ Z, int rows, int Dp, int Np, int CH)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int rt = (rows + TR - 1) / TR, ct = (Np + 127) >> 7;
+    const uint32_t yt_s = (uint32_t)__cvta_generic_to_shared(YT);
+    const uint32_t mt_s = MT_SHARED ? (uint32_t)__cvta_generic_to_shared(MT) : 0u;
+    for (int tile = warp; tile < rt * ct; tile += nw) {
+        const int tr = tile / ct, tc = tile - tr * ct;
+        const int rb = TR * tr, c = 128 * tc + 4 * lane;
+        const bool col_ok = c < Np;
+        float acc[TR][4];
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 2
+        for (int k = 0; k < Dp; ++k) {
+            const uint32_t ya = yt_s + 4u * (uint32_t)(k * CH + rb);
+            const float4 a0 = lds4(ya);
+            const float4 a1 = TR == 8 ? lds4(ya + 16u) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (col_ok) {
+                if (MT_SHARED) b = lds4(mt_s + 4u * (uint32_t)(k * Np + c));
+                else b = __ldg(reinterpret_cast<const float4*>(MT + (size_t)k * Np + c));
+            }
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+            for (int i = 0; i < TR; ++i) {
+                acc[i][0] = fmaf(av[i], b.x, acc[i][0]);
+                acc[i][1] = fmaf(av[i], b.y, acc[i][1]);
+                acc[i][2] = fmaf(av[i], b.z, acc[i][2]);
+                acc[i][3] = fmaf(av[i], b.w, acc[i][3]);
+            }
+        }
+        if (col_ok) {
+#pragma unroll
+            for (int i = 0; i < TR; ++i)
+                if (rb + i < rows)
+                    *reinterpret_cast<float4*>(Z + (size_t)(rb + i) * Np + c) =
+                        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        }
+    }
+}
+
+// 8-row tiles when they keep every warp busy, 4-row tiles otherwise.
+template <bool MT_SHARED>
+__device__ __forceinline__ void tile_gemm(const float* __restrict__ YT, const float* __restrict__ MT,
+                                          float* __restrict__ Z, int rows, int Dp, int Np, int CH)
+{
+    const int nw = blockDim.x >> 5, ct = (Np + 127) >> 7;
+    if (((rows + 7) >> 3) * ct >= nw) tile_gemm_t<MT_SHARED, 8>(YT, MT, Z, rows, Dp, Np, CH);
+    else tile_gemm_t<MT_SHARED, 4>(YT, MT, Z, rows, Dp, Np, CH);
+}
+
+// Segmented objective of one row by one warp (z[d * zs]): [0, s1) high-conditioned
+// elliptic, [s1, s2) chained Rosenbrock, [s2, D) Rastrigin cosine sum.
+__device__ __forceinline__ float seg_value(const float* z, int zs, const DevComp& C, const float* ew, int D)
+{
+    const int lane = threadIdx.x & 31;
+    float s = 0.f;
+    for (int d = lane; d < D; d += 32) {
+        const float v = z[(size_t)d * zs];
+        if (d < C.s1) {
+            s = fmaf(ew[d] * v, v, s);
+        } else if (d < C.s2) {
+            if (d + 1 < C.s2) {
+                const float a = z[(size_t)(d + 1) * zs] - v * v;
+                const float b = v - 1.f;
+                s += 100.f * a * a + b * b;
+            }
+        } else {
+            s += v * v - 10.f * cospif(2.f * v) + 10.f;
+        }
+    }
+    return warp_sum(s);
+}
+
+// Otsu between-class variance of one row by one warp (thresholds in lanes
+// 0..T-1), negated.  The float64 operations follow a fixed order with
+// explicit round-to-nearest intrinsics (no contraction) so that the value is
+// reproducible bit for bit.
+__device__ __forceinline__ double otsu_row(const float* x, int T, const long long* P0, const long long* P1,
+                           int* scratch)
+{
+    const int lane = threadIdx.x & 31;
+    int tv = 0;
+    if (lane < T) {
+        float f = floorf(x[lane]);
+        f = fminf(fmaxf(f, 0.f), 255.f);
+        tv = (int)f;
+    }
+    int rank = 0;
+    for (int i = 0; i < T; ++i) {
+        const int ti = __shfl_sync(0xffffffffu, tv, i);
+        if (ti < tv || (ti == tv && i < lane)) ++rank;
+    }
+    __syncwarp();
+    if (lane < T) scratch[rank] = tv;
+    __syncwarp();
+    double sigma = 0.0;
+    if (lane == 0) {
+        const long long N = P0[255], Ssum = P1[255];
+        const double muT = __ddiv_rn((double)Ssum, (double)N);
+        int prev = -1;
+        for (int c = 0; c <= T; ++c) {
+            const int hi = (c < T) ? scratch[c] : 255;
+            long long nc = 0, sc = 0;
+            if (hi > prev) {
+                nc = P0[hi] - (prev >= 0 ? P0[prev] : 0ll);
+                sc = P1[hi] - (prev >= 0 ? P1[prev] : 0ll);
+                prev = hi;
+            }
+            if (nc > 0) {
+                const double omega = __ddiv_rn((double)nc, (double)N);
+                const double mu = __ddiv_rn((double)sc, (double)nc);
+                const double dm = __dsub_rn(mu, muT);
+                double term = __dmul_rn(omega, dm);
+                term = __dmul_rn(term, dm);
+                sigma = __dadd_rn(sigma, term);
+            }
+        }
+    }
+    sigma = __shfl_sync(0xffffffffu, sigma, 0);
+    __syncwarp();
+    return -sigma;
+}
+
+// Evaluates the candidate rows Xc[0, rows) into rowF.  Called by the whole
+// CTA; ends synchronised.
+template <typename FitT>
+__device__ __forceinline__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S, int rows)
+{
+    const DevProblem& P = R.prob;
+    const int D = P.D, Dp = P.Dp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (P.kind == kOtsu) {
+        for (int row = warp; row < rows; row += nw) {
+            const double f = otsu_row(S.Xc + (size_t)row * Dp, D, S.P0, S.P1, S.otsu + warp * 32);
+            if (lane == 0) S.rowF[row] = (FitT)f;
+        }
+        __syncthreads();
+        return;
+    }
+    const int CH = R.plan.chunk, Np = P.Np;
+    for (int c = 0; c < P.ncomp; ++c) {
+        const DevComp& C = P.comp[c];
+        const float* o = (c == 0) ? S.o : C.o;
+        // YT[d][row] = x - o (zero beyond D)
+        for (int i = threadIdx.x; i < CH * Dp; i += blockDim.x) {
+            const int d = i / CH, row = i - d * CH;
+            S.Yc[i] = (d < D && row < rows) ? S.Xc[(size_t)row * Dp + d] - o[d] : 0.f;
+        }
+        __syncthreads();
+        if (C.MT) {
+            if (c == 0 && R.plan.mt_smem) tile_gemm<true>(S.Yc, S.MT, S.Zc, rows, Dp, Np, CH);
+            else tile_gemm<false>(S.Yc, C.MT, S.Zc, rows, Dp, Np, CH);
+            __syncthreads();
+        }
+        const float* ew = (c == 0) ? S.ew : C.ew;
+        for (int row = warp; row < rows; row += nw) {
+            const float v = C.MT ? seg_value(S.Zc + (size_t)row * Np, 1, C, ew, D)
+                                 : seg_value(S.Yc + row, CH, C, ew, D);
+            if (P.ncomp == 1) {
+                if (lane == 0) S.rowF[row] = (FitT)v;
+            } else {
+                float d2 = 0.f;
+                for (int d = lane; d < D; d += 32) {
+                    const float y = S.Yc[(size_t)d * CH + row];
+                    d2 = fmaf(y, y, d2);
+                }
+                d2 = warp_sum(d2);
+                if (lane == 0) {
+                    S.compG[row * kMaxComp + c] = v;
+                    S.compA[row * kMaxComp + c] = -d2 * C.inv_2Dsig2;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (P.ncomp > 1) {
+        // f = sum_k w_k (g_k + bias_k) / sum_k w_k, w_k = exp(a_k - max a).
+        for (int row = warp; row < rows; row += nw) {
+            const bool on = lane < P.ncomp;
+            const float a = on ? S.compA[row * kMaxComp + lane] : -INFINITY;
+            const float amax = warp_max(a);
+            const float w = on ? expf(a - amax) : 0.f;
+            const float gv = on ? S.compG[row * kMaxComp + lane] + P.comp[lane < kMaxComp ? lane : 0].bias : 0.f;
+            const float num = warp_sum(w * gv);
+            const float den = warp_sum(w);
+            if (lane == 0) S.rowF[row] = (FitT)(num / den);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------- state access
+template <typename T>
+__device__ __forceinline__ T ldst(const T* p, bool resident)
+{
+    return resident ? *p : __ldcg(p);
+}
+
+// ------------------------------------------------- candidate generation
+// Population initialisation (Algorithm 1): X_p = Xmin + U (Xmax - Xmin).
+template <typename FitT, int QPL>
+__device__ __forceinline__ void gen_init_row(const ApoRun& R, const Smem<FitT>& S, int p, int row)
+{
+    const int lane = threadIdx.x & 31;
+    const int D = R.prob.D, Dp = R.prob.Dp;
+    float* xc = S.Xc + (size_t)row * Dp;
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const int q = lane + 32 * j;
+        const int d0 = 2 * q;
+        if (d0 < D) {
+            const uint4 w = philox(0u, (uint32_t)p, (uint32_t)q, kSlotInit, R.seed, R.run);
+            xc[d0] = fmaf(u01(w.x), S.ub[d0] - S.lb[d0], S.lb[d0]);
+            if (d0 + 1 < D) xc[d0 + 1] = fmaf(u01(w.z), S.ub[d0 + 1] - S.lb[d0 + 1], S.lb[d0 + 1]);
+            else if (d0 + 1 < Dp) xc[d0 + 1] = 0.f;
+        } else if (d0 < Dp) {
+            xc[d0] = 0.f;
+            xc[d0 + 1] = 0.f;
+        }
+    }
+}
+
+// One candidate (rank r, 0-based) by one warp: mode selection (Eq. 12-13,
+// Algorithm 1), masks (Eq. 3, Eq. 5), dormancy (Eq. 1), reproduction
+// (Eq. 2), autotrophic (Eq. 6-7) or heterotrophic (Eq. 8-10) foraging, then
+// the bound clamp.  Writes row `row` of Xc (candidate) and of Xo (the old
+// position, kept for the greedy replacement).  The per-protozoon draws are
+// computed once per warp, one Philox call per lane; the gathered rows are
+// requested before the per-dimension draws and the mask selection so that
+// their latency overlaps that arithmetic.
+template <typename FitT, int QPL>
+__device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* __restrict__ X,
+                             const FitT* __restrict__ F, const uint32_t* perm, bool res, int t,
+                             int r, int row, int cand = 0)
+{
+    // candidate c of the surrogate-assisted form draws from slots | (c << 8);
+    // c = 0 is the plain candidate
+    const uint32_t cs = (uint32_t)cand << 8;
+    const int lane = threadIdx.x & 31;
+    const int D = R.prob.D, Dp = R.prob.Dp, ps = R.ps, np = R.np;
+    const uint32_t seed = R.seed, run = R.run;
+    // lane 0: SCAL, lane 1: SCAL2, lane 2 + k: PAIR k
+    uint32_t jslot = kSlotPair | cs, jd = (uint32_t)(lane - 2);
+    if (lane == 0) { jslot = kSlotScal | cs; jd = kAll; }
+    if (lane == 1) { jslot = kSlotScal2 | cs; jd = kAll; }
+    const uint4 jw = philox((uint32_t)t, (uint32_t)r, jd, jslot, seed, run);
+    uint4 sc, sc2;
+    sc.x = __shfl_sync(0xffffffffu, jw.x, 0); sc.y = __shfl_sync(0xffffffffu, jw.y, 0);
+    sc.z = __shfl_sync(0xffffffffu, jw.z, 0); sc.w = __shfl_sync(0xffffffffu, jw.w, 0);
+    sc2.x = __shfl_sync(0xffffffffu, jw.x, 1); sc2.y = __shfl_sync(0xffffffffu, jw.y, 1);
+    const int W = (ps + 31) >> 5;
+    const bool in_dr = (R.drmask[(size_t)t * W + (r >> 5)] >> (r & 31)) & 1u;
+    const uint32_t mm = m24p1(sc.x);
+    int mode;
+    if (in_dr) mode = (mm < R.thr_dr[r]) ? kDormancy : kReproduction;
+    else mode = (mm < R.thr_ah[t]) ? kAutotrophic : kHeterotrophic;
+    const bool forage = mode == kAutotrophic || mode == kHeterotrophic;
+
+    // rows from the snapshot: X_i, X_j (autotrophic) and the first pair
+    const int si = (int)perm[r];
+    int sj = si, sa = si, sb = si;
+    if (mode == kAutotrophic) {
+        sj = (int)perm[idx_draw(sc2.y, (uint32_t)ps)];
+        const uint32_t p0 = __shfl_sync(0xffffffffu, jw.x, 2), p1 = __shfl_sync(0xffffffffu, jw.y, 2);
+        sa = (int)perm[idx_draw(p0, (uint32_t)ps)];
+        sb = (int)perm[idx_draw(p1, (uint32_t)ps)];
+    } else if (mode == kHeterotrophic) {
+        sa = (int)perm[r - 1 < 0 ? 0 : r - 1];
+        sb = (int)perm[r + 1 > ps - 1 ? ps - 1 : r + 1];
+    }
+    float xi[2 * QPL], xj[2 * QPL], xa[2 * QPL], xb[2 * QPL];
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const int q = lane + 32 * j;
+        float2 vi = make_float2(0.f, 0.f), vj = vi, va = vi, vb = vi;
+        if (2 * q < D) {
+            vi = ldst(reinterpret_cast<const float2*>(X + (size_t)si * Dp) + q, res);
+            if (mode == kAutotrophic) vj = ldst(reinterpret_cast<const float2*>(X + (size_t)sj * Dp) + q, res);
+            if (forage) {
+                va = ldst(reinterpret_cast<const float2*>(X + (size_t)sa * Dp) + q, res);
+                vb = ldst(reinterpret_cast<const float2*>(X + (size_t)sb * Dp) + q, res);
+            }
+        }
+        xi[2 * j] = vi.x; xi[2 * j + 1] = vi.y;
+        xj[2 * j] = vj.x; xj[2 * j + 1] = vj.y;
+        xa[2 * j] = va.x; xa[2 * j + 1] = va.y;
+        xb[2 * j] = vb.x; xb[2 * j + 1] = vb.y;
+    }
+    float fa = 0.f, fb = 1.f;
+    if (forage) {
+        fa = (float)ldst(F + sa, res);
+        fb = (float)ldst(F + sb, res);
+    }
+    if (lane == 0) S.rowF[R.plan.chunk + row] = ldst(F + si, res);   // old fitness for the greedy step
+
+    // per-dimension draws and the mask (independent of the gathered rows)
+    uint32_t A[2 * QPL], B[2 * QPL];
+    uint32_t valid = 0;
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const int q = lane + 32 * j;
+        if (2 * q < D) {
+            const uint4 w = philox((uint32_t)t, (uint32_t)r, (uint32_t)q, kSlotDim | cs, seed, run);
+            A[2 * j] = w.x; B[2 * j] = w.y; A[2 * j + 1] = w.z; B[2 * j + 1] = w.w;
+            valid |= 1u << (2 * j);
+            if (2 * q + 1 < D) valid |= 1u << (2 * j + 1);
+        } else {
+            A[2 * j] = B[2 * j] = A[2 * j + 1] = B[2 * j + 1] = 0u;
+        }
+    }
+    uint32_t mask = 0;
+    if (mode == kReproduction) {
+        const int k = (int)(((unsigned long long)D * m24p1(sc2.x) + 0xFFFFFFull) >> 24);
+        mask = warp_kselect<QPL>(B, valid, k);
+    } else if (forage) {
+        const int k = (D * (r + 1) + ps - 1) / ps;
+        mask = warp_kselect<QPL>(B, valid, k);
+    }
+
+    // Eq. 7 / Eq. 10 weights and the pair sums
+    float acc[2 * QPL];
+    if (forage) {
+        const float w = expf(-fabsf(fa / (fb + kEps)));
+#pragma unroll
+        for (int e = 0; e < 2 * QPL; ++e) acc[e] = w * (xa[e] - xb[e]);
+        for (int k = 2; k <= np; ++k) {
+            if (mode == kAutotrophic) {
+                uint32_t p0, p1;
+                if (k + 1 < 32) {
+                    p0 = __shfl_sync(0xffffffffu, jw.x, k + 1);
+                    p1 = __shfl_sync(0xffffffffu, jw.y, k + 1);
+                } else {
+                    const uint4 pr = philox((uint32_t)t, (uint32_t)r, (uint32_t)(k - 1), kSlotPair | cs, seed, run);
+                    p0 = pr.x;
+                    p1 = pr.y;
+                }
+                sa = (int)perm[idx_draw(p0, (uint32_t)ps)];
+                sb = (int)perm[idx_draw(p1, (uint32_t)ps)];
+            } else {
+                sa = (int)perm[r - k < 0 ? 0 : r - k];
+                sb = (int)perm[r + k > ps - 1 ? ps - 1 : r + k];
+            }
+            const float w2 = expf(-fabsf((float)ldst(F + sa, res) / ((float)ldst(F + sb, res) + kEps)));
+#pragma unroll
+            for (int j = 0; j < QPL; ++j) {
+                const int q = lane + 32 * j;
+                if (2 * q < D) {
+                    const float2 va = ldst(reinterpret_cast<const float2*>(X + (size_t)sa * Dp) + q, res);
+                    const float2 vb = ldst(reinterpret_cast<const float2*>(X + (size_t)sb * Dp) + q, res);
+                    acc[2 * j] = fmaf(w2, va.x - vb.x, acc[2 * j]);
+                    acc[2 * j + 1] = fmaf(w2, va.y - vb.y, acc[2 * j + 1]);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 2 * QPL; ++e) acc[e] = 0.f;
+    }
+    const float inv_np = 1.f / (float)np;
+    const float ff = forage ? u01(sc.y) * R.fsc[t] : 0.f;
+    const float s = sign_draw(sc.z);
+    const float rho = u01(sc.w);
+    const float nsc = R.nsc[t];
+
+    float* xc = S.Xc + (size_t)row * Dp;
+    float* xo = S.Xo + (size_t)row * Dp;
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const int q = lane + 32 * j;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int d = 2 * q + e;
+            const int sl = 2 * j + e;
+            if (d < D) {
+                const float lb = S.lb[d], ub = S.ub[d];
+                const bool mk = (mask >> sl) & 1u;
+                const float x0 = xi[sl];
+                float x = x0;
+                if (mode == kDormancy) {
+                    x = fmaf(u01(A[sl]), ub - lb, lb);                          // Eq. 1
+                } else if (mk) {
+                    if (mode == kReproduction) {
+                        x = x0 + s * rho * fmaf(u01(A[sl]), ub - lb, lb);       // Eq. 2
+                    } else if (mode == kAutotrophic) {
+                        x = x0 + ff * (xj[sl] - x0 + acc[sl] * inv_np);         // Eq. 6
+                    } else {
+                        const float xnear = (1.f + s * u01(A[sl]) * nsc) * x0;  // Eq. 9
+                        x = x0 + ff * (xnear - x0 + acc[sl] * inv_np);          // Eq. 8
+                    }
+                }
+                xc[d] = fminf(fmaxf(x, lb), ub);
+                xo[d] = x0;
+            } else if (d < Dp) {
+                xc[d] = 0.f;
+                xo[d] = 0.f;
+            }
+        }
+    }
+}
+
+
+}  // namespace apo

@@ -349,3 +349,460 @@ extern "C" apo_status apo_mlp_get_params(const apo_mlp* M, float* W1, float* b1,
     if (b3) SUR_CUDA(cudaMemcpy(b3, M->b3, 4, cudaMemcpyDeviceToHost));
     return APO_OK;
 }
+
+// ===================================================== surrogate-assisted APO
+#include "apo_path.cuh"
+
+namespace {
+
+constexpr int kSurThreads = 256;
+
+// Stable sort of the population by (F, previous rank): perm_out[rank] = slot;
+// curve[t - 1] = the smallest fitness.  One CTA, keys in shared memory.
+__global__ void __launch_bounds__(1024) surr_sort_kernel(int ps, int ps_pad, const float* __restrict__ F,
+                                                         const uint32_t* __restrict__ perm_prev,
+                                                         uint32_t* __restrict__ perm_out, float* curve, int t)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    using KO = KeyOf<float>;
+    KO::T* keys = reinterpret_cast<KO::T*>(dyn);
+    for (int r = threadIdx.x; r < ps_pad; r += blockDim.x)
+        keys[r] = r < ps ? KO::make(F[perm_prev[r]], (uint32_t)r) : KO::pad();
+    __syncthreads();
+    bitonic_sort<KO>(keys, ps_pad);
+    for (int r = threadIdx.x; r < ps; r += blockDim.x) perm_out[r] = perm_prev[KO::idx(keys[r])];
+    if (threadIdx.x == 0 && curve) curve[t - 1] = F[perm_prev[KO::idx(keys[0])]];
+}
+
+template <int QPL>
+__device__ void surr_setup(const ApoRun* run, ApoRun& R, unsigned char* smem, Smem<float>& S,
+                           const uint32_t* __restrict__ perm, bool copy_perm)
+{
+    const unsigned long long* s = reinterpret_cast<const unsigned long long*>(run);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(&R);
+    for (int i = threadIdx.x; i < (int)(sizeof(ApoRun) / 8); i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+    S = carve<float>(smem, R.plan);
+    load_constants<float>(R, S);
+    if (copy_perm)
+        for (int r = threadIdx.x; r < R.ps; r += blockDim.x) S.perm[0][r] = perm[r];
+    __syncthreads();
+}
+
+// Initial population (Algorithm 1): X_p = Xmin + U (Xmax - Xmin), F = f(X).
+template <int QPL>
+__global__ void __launch_bounds__(kSurThreads) surr_init_kernel(const ApoRun* __restrict__ run, float* X, float* F)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ApoRun R;
+    Smem<float> S;
+    surr_setup<QPL>(run, R, smem, S, nullptr, false);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int Dp = R.prob.Dp, CH = R.plan.chunk;
+    for (int c0 = blockIdx.x * CH; c0 < R.ps; c0 += gridDim.x * CH) {
+        const int rows = min(CH, R.ps - c0);
+        for (int row = warp; row < rows; row += nw) gen_init_row<float, QPL>(R, S, c0 + row, row);
+        __syncthreads();
+        eval_chunk<float>(R, S, rows);
+        for (int row = warp; row < rows; row += nw) {
+            for (int d = lane; d < Dp; d += 32) X[(size_t)(c0 + row) * Dp + d] = S.Xc[(size_t)row * Dp + d];
+            if (lane == 0) F[c0 + row] = S.rowF[row];
+        }
+        __syncthreads();
+    }
+}
+
+// k candidates per protozoon (rank r, candidate c = q mod k): the rows of
+// Xcand [ps k][Dp] and the network inputs Xin [ps k][Kp] (bf16, scaled to
+// [-1, 1] by the bounds).
+template <int QPL>
+__global__ void __launch_bounds__(kSurThreads) surr_gen_kernel(const ApoRun* __restrict__ run, int k, int t,
+                                                              const uint32_t* __restrict__ perm,
+                                                              const float* __restrict__ X, const float* __restrict__ F,
+                                                              float* __restrict__ Xcand, __nv_bfloat16* __restrict__ Xin,
+                                                              int Kp)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ApoRun R;
+    Smem<float> S;
+    surr_setup<QPL>(run, R, smem, S, perm, true);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int D = R.prob.D, Dp = R.prob.Dp, CH = R.plan.chunk;
+    const int nrow = R.ps * k;
+    for (int c0 = blockIdx.x * CH; c0 < nrow; c0 += gridDim.x * CH) {
+        const int rows = min(CH, nrow - c0);
+        for (int row = warp; row < rows; row += nw) {
+            const int q = c0 + row, r = q / k, c = q - r * k;
+            gen_step_row<float, QPL>(R, S, X, F, S.perm[0], false, t, r, row, c);
+            __syncwarp();
+            for (int d = lane; d < Dp; d += 32) Xcand[(size_t)q * Dp + d] = S.Xc[(size_t)row * Dp + d];
+            if (Xin)
+                for (int d = lane; d < Kp; d += 32) {
+                    float v = 0.f;
+                    if (d < D) v = 2.f * (S.Xc[(size_t)row * Dp + d] - S.lb[d]) / (S.ub[d] - S.lb[d]) - 1.f;
+                    Xin[(size_t)q * Kp + d] = __float2bfloat16(v);
+                }
+        }
+        __syncthreads();
+    }
+}
+
+// For every rank: the best-scored candidate (candidate 0 when kk == 1) is
+// evaluated exactly and replaces the protozoon iff it improves it (Algorithm
+// 1); the evaluation is appended to the archive.
+template <int QPL>
+__global__ void __launch_bounds__(kSurThreads) surr_select_kernel(
+    const ApoRun* __restrict__ run, int k, int kk, const uint32_t* __restrict__ perm, const float* __restrict__ X,
+    const float* __restrict__ F, const float* __restrict__ Xcand, const float* __restrict__ score,
+    float* __restrict__ Xn, float* __restrict__ Fn, __nv_bfloat16* __restrict__ Xa, float* __restrict__ Fa, int Kp,
+    long long arch_pos, int arch_cap, float* __restrict__ pred, float* __restrict__ truth)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ApoRun R;
+    __shared__ int s_c[64];
+    Smem<float> S;
+    surr_setup<QPL>(run, R, smem, S, nullptr, false);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int D = R.prob.D, Dp = R.prob.Dp, CH = R.plan.chunk, ps = R.ps;
+    for (int c0 = blockIdx.x * CH; c0 < ps; c0 += gridDim.x * CH) {
+        const int rows = min(CH, ps - c0);
+        for (int row = warp; row < rows; row += nw) {
+            const int r = c0 + row;
+            int best = 0;
+            if (kk > 1) {
+                float bv = INFINITY;
+                for (int c = 0; c < kk; ++c) {
+                    const float v = score[(size_t)r * k + c];
+                    if (v < bv) { bv = v; best = c; }
+                }
+            }
+            if (lane == 0) {
+                s_c[row] = best;
+                S.rowF[CH + row] = F[perm[r]];
+            }
+            for (int d = lane; d < Dp; d += 32) S.Xc[(size_t)row * Dp + d] = Xcand[((size_t)r * k + best) * Dp + d];
+        }
+        __syncthreads();
+        eval_chunk<float>(R, S, rows);
+        for (int row = warp; row < rows; row += nw) {
+            const int r = c0 + row, slot = (int)perm[r];
+            const float fo = S.rowF[CH + row], fn = S.rowF[row];
+            const bool acc = fn < fo;
+            for (int d = lane; d < Dp; d += 32)
+                Xn[(size_t)slot * Dp + d] = acc ? S.Xc[(size_t)row * Dp + d] : X[(size_t)slot * Dp + d];
+            const long long pos = (arch_pos + r) % arch_cap;
+            for (int d = lane; d < Kp; d += 32) {
+                float v = 0.f;
+                if (d < D) v = 2.f * (S.Xc[(size_t)row * Dp + d] - S.lb[d]) / (S.ub[d] - S.lb[d]) - 1.f;
+                Xa[(size_t)pos * Kp + d] = __float2bfloat16(v);
+            }
+            if (lane == 0) {
+                Fn[slot] = acc ? fn : fo;
+                Fa[pos] = fn;
+                pred[r] = kk > 1 ? score[(size_t)r * k + s_c[row]] : NAN;
+                truth[r] = fn;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Training targets: standardised log1p(F - min F) over the archive.
+__global__ void __launch_bounds__(1024) surr_targets_kernel(int n, const float* __restrict__ Fa, float* __restrict__ tgt)
+{
+    __shared__ double red[1024];
+    __shared__ double s_min, s_mean, s_std;
+    double mn = INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) mn = fmin(mn, (double)Fa[i]);
+    red[threadIdx.x] = mn;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s_min = red[0];
+    __syncthreads();
+    double s = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = log1p((double)Fa[i] - s_min);
+        s += v;
+        s2 += v * v;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s_mean = red[0] / n;
+    __syncthreads();
+    red[threadIdx.x] = s2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s_std = sqrt(fmax(red[0] / n - s_mean * s_mean, 1e-12));
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        tgt[i] = (float)((log1p((double)Fa[i] - s_min) - s_mean) / s_std);
+}
+
+double spearman(const std::vector<float>& a, const std::vector<float>& b)
+{
+    const size_t n = a.size();
+    auto ranks = [](const std::vector<float>& v) {
+        std::vector<size_t> idx(v.size());
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t i, size_t j) { return v[i] < v[j]; });
+        std::vector<double> r(v.size());
+        for (size_t i = 0; i < idx.size(); ++i) r[idx[i]] = (double)i;
+        return r;
+    };
+    const std::vector<double> ra = ranks(a), rb = ranks(b);
+    double ma = 0, mb = 0;
+    for (size_t i = 0; i < n; ++i) { ma += ra[i]; mb += rb[i]; }
+    ma /= n; mb /= n;
+    double sab = 0, saa = 0, sbb = 0;
+    for (size_t i = 0; i < n; ++i) {
+        sab += (ra[i] - ma) * (rb[i] - mb);
+        saa += (ra[i] - ma) * (ra[i] - ma);
+        sbb += (rb[i] - mb) * (rb[i] - mb);
+    }
+    return (saa > 0 && sbb > 0) ? sab / std::sqrt(saa * sbb) : 0.0;
+}
+
+}  // namespace
+
+namespace {
+
+template <int QPL>
+cudaError_t launch_surr(int which, dim3 grid, size_t smem, cudaStream_t st, const ApoRun* run, int k, int kk, int t,
+                        const uint32_t* perm, const float* X, const float* F, float* Xcand, __nv_bfloat16* Xin,
+                        int Kp, const float* score, float* Xn, float* Fn, __nv_bfloat16* Xa, float* Fa,
+                        long long arch_pos, int arch_cap, float* pred, float* truth)
+{
+    if (which == 0) {
+        cudaError_t e = cudaFuncSetAttribute(surr_init_kernel<QPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        surr_init_kernel<QPL><<<grid, kSurThreads, smem, st>>>(run, Xn, Fn);
+    } else if (which == 1) {
+        cudaError_t e = cudaFuncSetAttribute(surr_gen_kernel<QPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        surr_gen_kernel<QPL><<<grid, kSurThreads, smem, st>>>(run, k, t, perm, X, F, Xcand, Xin, Kp);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(surr_select_kernel<QPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        surr_select_kernel<QPL><<<grid, kSurThreads, smem, st>>>(run, k, kk, perm, X, F, Xcand, score, Xn, Fn, Xa, Fa,
+                                                                 Kp, arch_pos, arch_cap, pred, truth);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surr_q(int qpl, int which, dim3 grid, size_t smem, cudaStream_t st, const ApoRun* run, int k, int kk,
+                          int t, const uint32_t* perm, const float* X, const float* F, float* Xcand,
+                          __nv_bfloat16* Xin, int Kp, const float* score, float* Xn, float* Fn, __nv_bfloat16* Xa,
+                          float* Fa, long long arch_pos, int arch_cap, float* pred, float* truth)
+{
+    switch (qpl) {
+    case 1: return launch_surr<1>(which, grid, smem, st, run, k, kk, t, perm, X, F, Xcand, Xin, Kp, score, Xn, Fn, Xa, Fa, arch_pos, arch_cap, pred, truth);
+    case 2: return launch_surr<2>(which, grid, smem, st, run, k, kk, t, perm, X, F, Xcand, Xin, Kp, score, Xn, Fn, Xa, Fa, arch_pos, arch_cap, pred, truth);
+    default: return launch_surr<4>(which, grid, smem, st, run, k, kk, t, perm, X, F, Xcand, Xin, Kp, score, Xn, Fn, Xa, Fa, arch_pos, arch_cap, pred, truth);
+    }
+}
+
+}  // namespace
+
+#include "apo_plan.h"
+
+extern "C" apo_status apo_run_surrogate(const apo_problem* P, const apo_params* p, const apo_surrogate_params* sp,
+                                        void* stream, float* best_x, double* best_f, float* curve,
+                                        apo_surrogate_stats* stats)
+{
+    if (!P || !p || !sp || !best_x || !best_f) { apo::set_last_error("apo_run_surrogate: NULL argument"); return APO_ERR_INVALID_ARG; }
+    if (P->kind == APO_OBJ_OTSU) { apo::set_last_error("apo_run_surrogate: float objectives only"); return APO_ERR_UNSUPPORTED; }
+    if (p->ps < 2 || p->np < 1 || 2 * p->np >= p->ps || !(p->pf_max >= 0.0 && p->pf_max <= 1.0) || p->max_iter < 1 ||
+        (p->pdr_form != 0 && p->pdr_form != 1)) {
+        apo::set_last_error("apo_run_surrogate: params out of range");
+        return APO_ERR_INVALID_ARG;
+    }
+    if (p->ps > 4096) { apo::set_last_error("apo_run_surrogate: ps above 4096"); return APO_ERR_UNSUPPORTED; }
+    const int k = sp->k, R_every = sp->retrain_every;
+    if (k < 1 || k > 32 || R_every < 1 || sp->archive_cap < p->ps || sp->train_steps < 0 || sp->batch < 1) {
+        apo::set_last_error("apo_run_surrogate: surrogate params out of range (1 <= k <= 32, retrain_every >= 1, "
+                            "archive_cap >= ps, batch >= 1)");
+        return APO_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int ps = p->ps, T = p->max_iter, D = P->D, Dp = P->Dp;
+    const int ps_pad = plan_pow2(ps);
+    const int qpl = D <= 64 ? 1 : (D <= 128 ? 2 : 4);
+    int* status = device_status_word();
+    if (!status) { apo::set_last_error("status word allocation failed"); return APO_ERR_OOM; }
+
+    apo_mlp* M = nullptr;
+    apo_status rc = apo_mlp_create(D, sp->net_seed, &M);
+    if (rc != APO_OK) return rc;
+    if (M->cap < ps * k) {
+        cudaFree(M->mem);
+        rc = mlp_alloc(M, ps * k);
+        if (rc != APO_OK) { delete M; return rc; }
+        // re-initialise the parameters of the larger allocation
+        apo_mlp* tmp = nullptr;
+        rc = apo_mlp_create(D, sp->net_seed, &tmp);
+        if (rc != APO_OK) { apo_mlp_destroy(M); return rc; }
+        cudaMemcpy(M->W1, tmp->W1, (size_t)M->Kp * kH * 4, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(M->W2, tmp->W2, (size_t)kH * kH * 4, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(M->w3, tmp->w3, kH * 4, cudaMemcpyDeviceToDevice);
+        apo_mlp_destroy(tmp);
+        refresh_bf16(M, 0);
+    }
+    const int Kp = M->Kp;
+    const SmemPlan plan = choose_plan(P, ps, false, false, 232448 - 2048);
+
+    // workspace
+    const int W = (ps + 31) / 32;
+    const int acap = sp->archive_cap;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { off = (off + 255) / 256 * 256; const size_t at = off; off += bytes; return at; };
+    const size_t o_run = take(sizeof(ApoRun)), o_offs = take(8), o_dr = take((size_t)(T + 1) * W * 4);
+    const size_t o_x0 = take((size_t)ps * Dp * 4), o_x1 = take((size_t)ps * Dp * 4);
+    const size_t o_f0 = take((size_t)ps * 4), o_f1 = take((size_t)ps * 4);
+    const size_t o_p0 = take((size_t)ps * 4), o_p1 = take((size_t)ps * 4);
+    const size_t o_xc = take((size_t)ps * k * Dp * 4), o_xa = take((size_t)acap * Kp * 2);
+    const size_t o_fa = take((size_t)acap * 4), o_tg = take((size_t)acap * 4);
+    const size_t o_pr = take((size_t)ps * 4), o_tr = take((size_t)ps * 4), o_cv = take((size_t)(T + 1) * 4);
+    void* ws = nullptr;
+    cudaError_t e = cudaMalloc(&ws, off);
+    if (e != cudaSuccess) { apo_mlp_destroy(M); apo::set_last_error("apo_run_surrogate: workspace allocation failed"); return APO_ERR_OOM; }
+    unsigned char* b = static_cast<unsigned char*>(ws);
+    auto fail = [&](apo_status s, const char* msg) {
+        if (msg) apo::set_last_error(msg);
+        cudaStreamSynchronize(st);
+        cudaFree(ws);
+        apo_mlp_destroy(M);
+        return s;
+    };
+
+    ApoRun R;
+    std::memset(&R, 0, sizeof(R));
+    R.prob = P->dev;
+    R.plan = plan;
+    R.ps = ps; R.np = p->np; R.T = T; R.pdr_form = p->pdr_form; R.pf_max = p->pf_max;
+    R.seed = p->seed; R.run = p->run; R.t_begin = 1; R.t_end = T; R.flags = kFlagInit; R.g = 1;
+    if (sched_tables(ps, p->pdr_form, T, &R.thr_dr, &R.thr_ah, &R.fsc, &R.nsc) != APO_OK)
+        return fail(APO_ERR_CUDA, nullptr);
+    R.drmask = reinterpret_cast<const uint32_t*>(b + o_dr);
+    const int offs[2] = {0, T};
+    std::vector<uint32_t> ident(ps);
+    std::iota(ident.begin(), ident.end(), 0u);
+    e = cudaMemcpyAsync(b + o_run, &R, sizeof(R), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_offs, offs, 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_p0, ident.data(), (size_t)ps * 4, cudaMemcpyHostToDevice, st);
+    const ApoRun* d_run = reinterpret_cast<const ApoRun*>(b + o_run);
+    if (e == cudaSuccess) e = launch_dr(d_run, reinterpret_cast<const int*>(b + o_offs), 1, T, ps_pad, st);
+    if (e != cudaSuccess) return fail(APO_ERR_CUDA, "apo_run_surrogate: set-up failed");
+
+    float* X[2] = {reinterpret_cast<float*>(b + o_x0), reinterpret_cast<float*>(b + o_x1)};
+    float* F[2] = {reinterpret_cast<float*>(b + o_f0), reinterpret_cast<float*>(b + o_f1)};
+    uint32_t* pm[2] = {reinterpret_cast<uint32_t*>(b + o_p0), reinterpret_cast<uint32_t*>(b + o_p1)};
+    float* Xcand = reinterpret_cast<float*>(b + o_xc);
+    __nv_bfloat16* Xa = reinterpret_cast<__nv_bfloat16*>(b + o_xa);
+    float* Fa = reinterpret_cast<float*>(b + o_fa);
+    float* tgt = reinterpret_cast<float*>(b + o_tg);
+    float* pred = reinterpret_cast<float*>(b + o_pr);
+    float* truth = reinterpret_cast<float*>(b + o_tr);
+    float* d_curve = reinterpret_cast<float*>(b + o_cv);
+    const size_t smem = plan.total;
+    const int grid_rows = (ps + plan.chunk - 1) / plan.chunk;
+    const size_t sort_smem = (size_t)ps_pad * 8;
+    if (sort_smem > 48 * 1024) cudaFuncSetAttribute(surr_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
+
+    cudaEvent_t t_all0, t_all1, tr0, tr1;
+    cudaEventCreate(&t_all0); cudaEventCreate(&t_all1); cudaEventCreate(&tr0); cudaEventCreate(&tr1);
+    cudaEventRecord(t_all0, st);
+    // initial population, evaluated and archived
+    e = launch_surr_q(qpl, 0, dim3(grid_rows), smem, st, d_run, 1, 1, 0, pm[0], nullptr, nullptr, nullptr, nullptr, Kp,
+                      nullptr, X[0], F[0], nullptr, nullptr, 0, acap, nullptr, nullptr);
+    if (e != cudaSuccess) return fail(APO_ERR_CUDA, "apo_run_surrogate: init launch failed");
+    long long arch_count = 0;   // the initial population is not archived (no candidate image)
+    int cur = 0, pc = 0;
+    bool screening = false;
+    apo_surrogate_stats S = {};
+    S.true_evals = ps;
+    double train_ms = 0.0;
+    for (int t = 1; t <= T; ++t) {
+        surr_sort_kernel<<<1, 1024, sort_smem, st>>>(ps, ps_pad, F[cur], pm[pc], pm[pc ^ 1], d_curve, t);
+        pc ^= 1;
+        const int kk = screening ? k : 1;
+        e = launch_surr_q(qpl, 1, dim3(std::max(1, std::min(1024, (ps * kk + plan.chunk - 1) / plan.chunk))), smem, st,
+                          d_run, kk, kk, t, pm[pc], X[cur], F[cur], Xcand, kk > 1 ? M->Xb : nullptr, Kp, nullptr,
+                          nullptr, nullptr, nullptr, nullptr, 0, acap, nullptr, nullptr);
+        if (e != cudaSuccess) return fail(APO_ERR_CUDA, "apo_run_surrogate: candidate launch failed");
+        if (kk > 1) {
+            rc = mlp_forward_rows(M, ps * kk, st);
+            if (rc != APO_OK) return fail(rc, nullptr);
+        }
+        e = launch_surr_q(qpl, 2, dim3(grid_rows), smem, st, d_run, kk, kk, t, pm[pc], X[cur], F[cur], Xcand, nullptr,
+                          Kp, M->y, X[cur ^ 1], F[cur ^ 1], Xa, Fa, arch_count, acap, pred, truth);
+        if (e != cudaSuccess) return fail(APO_ERR_CUDA, "apo_run_surrogate: select launch failed");
+        arch_count += ps;
+        cur ^= 1;
+        S.true_evals += ps;
+        S.screened += (long long)ps * kk;
+        if (kk > 1) ++S.screening_iters;
+        if (t % R_every == 0 && t < T) {
+            // error monitor of the last screened batch, then retrain
+            if (screening) {
+                std::vector<float> hp(ps), ht(ps);
+                cudaMemcpyAsync(hp.data(), pred, (size_t)ps * 4, cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(ht.data(), truth, (size_t)ps * 4, cudaMemcpyDeviceToHost, st);
+                cudaStreamSynchronize(st);
+                S.last_rank_corr = spearman(hp, ht);
+            }
+            const int n = (int)std::min<long long>(arch_count, acap);
+            surr_targets_kernel<<<1, 1024, 0, st>>>(n, Fa, tgt);
+            cudaEventRecord(tr0, st);
+            rc = mlp_train_rows(M, Xa, tgt, n, sp->train_steps, sp->batch, sp->lr, sp->net_seed + (uint32_t)t, st);
+            cudaEventRecord(tr1, st);
+            if (rc != APO_OK) return fail(rc, nullptr);
+            ++S.retrains;
+            const bool was = screening;
+            screening = !was || S.last_rank_corr >= sp->min_rank_corr;
+            cudaEventSynchronize(tr1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, tr0, tr1);
+            train_ms += ms;
+        } else if (!screening && S.retrains > 0) {
+            ++S.fallback_iters;
+        }
+    }
+    // the best of the final population
+    surr_sort_kernel<<<1, 1024, sort_smem, st>>>(ps, ps_pad, F[cur], pm[pc], pm[pc ^ 1], d_curve, T + 1);
+    pc ^= 1;
+    uint32_t bslot = 0;
+    e = cudaMemcpyAsync(&bslot, pm[pc], 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    std::vector<float> xb(Dp);
+    float fb = 0.f;
+    if (e == cudaSuccess) e = cudaMemcpy(xb.data(), X[cur] + (size_t)bslot * Dp, (size_t)Dp * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&fb, F[cur] + bslot, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && curve) e = cudaMemcpy(curve, d_curve, (size_t)(T + 1) * 4, cudaMemcpyDeviceToHost);
+    cudaEventRecord(t_all1, st);
+    cudaEventSynchronize(t_all1);
+    float all_ms = 0.f;
+    cudaEventElapsedTime(&all_ms, t_all0, t_all1);
+    cudaEventDestroy(t_all0); cudaEventDestroy(t_all1); cudaEventDestroy(tr0); cudaEventDestroy(tr1);
+    if (e != cudaSuccess) return fail(APO_ERR_CUDA, "apo_run_surrogate: result copy failed");
+    std::memcpy(best_x, xb.data(), sizeof(float) * D);
+    *best_f = fb;
+    S.train_ms = train_ms;
+    S.total_ms = all_ms;
+    if (stats) *stats = S;
+    cudaFree(ws);
+    apo_mlp_destroy(M);
+    int h = 0;
+    cudaMemcpy(&h, status, 4, cudaMemcpyDeviceToHost);
+    if (h != 0) { apo::set_last_error("a device-side wait exceeded its limit"); return (apo_status)h; }
+    return APO_OK;
+}

@@ -1,0 +1,46 @@
+"""Surrogate-assisted APO on the GPU: with one candidate per protozoon it is
+the plain method draw for draw (bit-identical curve and best), and its
+bookkeeping (true evaluations, retrains) matches its parameters."""
+import numpy as np
+import pytest
+
+from paper_2510_14982_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def apo():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_14982_gb300 import apo as m
+    return m
+
+
+@pytest.mark.parametrize("mk,ps,T", [(lambda: inputs.single_rastrigin(0), 20, 80),
+                                     (lambda: inputs.composition(D=20, seed=2), 64, 40)])
+def test_one_candidate_is_the_plain_method(apo, mk, ps, T):
+    spec = mk()
+    prob = apo.problem_from_spec(spec)
+    prm = apo.apo_params_make(ps, 1, 0.1, T, 7)
+    xp, fp, cp = apo.apo_run(prob, prm)
+    xs, fs, cs, st = apo.apo_run_surrogate(prob, prm, apo.surrogate_params(k=1, retrain_every=10, train_steps=5))
+    assert fs == fp
+    np.testing.assert_array_equal(cs, cp)
+    np.testing.assert_array_equal(xs, xp)
+    assert st["true_evals"] == ps * (T + 1)
+    assert st["screened"] == ps * T
+
+
+def test_screening_bookkeeping(apo):
+    spec = inputs.composition(D=20, seed=3)
+    prob = apo.problem_from_spec(spec)
+    ps, T, k = 64, 45, 4
+    _, f, c, st = apo.apo_run_surrogate(prob, apo.apo_params_make(ps, 1, 0.1, T, 1),
+                                        apo.surrogate_params(k=k, retrain_every=10, train_steps=20, batch=256))
+    assert st["true_evals"] == ps * (T + 1)
+    assert st["retrains"] == 4
+    assert st["screening_iters"] + 10 + st["fallback_iters"] == T
+    assert st["screened"] == ps * (T - st["screening_iters"]) + ps * k * st["screening_iters"]
+    assert np.all(np.diff(c) <= 0) and c[-1] == np.float32(f)
