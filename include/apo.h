@@ -240,8 +240,9 @@ apo_status apo_mlp_train(apo_mlp* mlp, const float* d_X, const float* d_t, int n
  * evaluated exactly and goes through the greedy replacement of Algorithm 1.
  * Exact evaluations fill a ring-buffer archive of archive_cap rows (inputs
  * scaled to [-1, 1] by the bounds, targets the standardised
- * log1p(F - min F)); every retrain_every iterations the network takes
- * train_steps Adam steps on batches of `batch` archive rows.  Screening
+ * log1p(F - min F) over the training window); every retrain_every
+ * iterations the network takes train_steps Adam steps on batches of `batch`
+ * rows drawn from the most recent train_window archive rows.  Screening
  * starts after the first retrain and stops, until the next retrain, when the
  * Spearman rank correlation between predicted and true fitness of the last
  * screened batch is below min_rank_corr (the plain method is the fallback).
@@ -256,6 +257,8 @@ typedef struct apo_surrogate_params {
     float lr;             /* Adam learning rate                         */
     float min_rank_corr;  /* screening threshold on Spearman correlation */
     uint32_t net_seed;    /* network initialisation and batch sampling  */
+    int train_window;     /* retrain on the most recent train_window archive rows
+                             (targets standardised over them); 0 = the whole archive */
 } apo_surrogate_params;
 
 typedef struct apo_surrogate_stats {

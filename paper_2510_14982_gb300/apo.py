@@ -54,7 +54,8 @@ class apo_batch_options(C.Structure):
 
 class apo_surrogate_params(C.Structure):
     _fields_ = [("k", C.c_int), ("retrain_every", C.c_int), ("archive_cap", C.c_int), ("train_steps", C.c_int),
-                ("batch", C.c_int), ("lr", C.c_float), ("min_rank_corr", C.c_float), ("net_seed", C.c_uint32)]
+                ("batch", C.c_int), ("lr", C.c_float), ("min_rank_corr", C.c_float), ("net_seed", C.c_uint32),
+                ("train_window", C.c_int)]
 
 
 class apo_surrogate_stats(C.Structure):
@@ -362,9 +363,9 @@ class Mlp:
 
 
 def surrogate_params(k=8, retrain_every=10, archive_cap=50000, train_steps=100, batch=1024, lr=1e-3,
-                     min_rank_corr=0.3, net_seed=0):
+                     min_rank_corr=0.3, net_seed=0, train_window=0):
     return apo_surrogate_params(int(k), int(retrain_every), int(archive_cap), int(train_steps), int(batch), float(lr),
-                                float(min_rank_corr), int(net_seed) & 0xFFFFFFFF)
+                                float(min_rank_corr), int(net_seed) & 0xFFFFFFFF, int(train_window))
 
 
 def apo_run_surrogate(prob: Problem, params: apo_params, sp: apo_surrogate_params, stream=None, want_curve=True):

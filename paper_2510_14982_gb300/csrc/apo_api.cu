@@ -54,6 +54,8 @@ constexpr size_t kSmemMax = 232448 - 2048;  // dynamic part; the kernels use < 1
 constexpr int kQueueMaxPs = 1024;
 // Minimum protozoa per CTA in grid mode.
 constexpr int kGridMinRows = 8;
+// A run launched alone uses the grid kernel from this population size on.
+constexpr int kGridSingleMinPs = 128;
 
 // Optional timing events around the iteration-loop kernels.
 cudaEvent_t g_ev_before = nullptr, g_ev_after = nullptr;
@@ -250,7 +252,7 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
             comps[k].bias = (float)obj->comp_bias[k];
         }
     }
-    size_t off_p0 = 0, off_p1 = 0, off_hist = 0;
+    size_t off_p0 = 0, off_p1 = 0, off_hist = 0, off_tab = 0;
     if (kind == APO_OBJ_OTSU) {
         std::vector<long long> p0(256, 0), p1(256, 0);
         if (!obj->hist_on_device) {
@@ -265,6 +267,7 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
         off_p0 = add(p0.data(), 256 * 8);
         off_p1 = add(p1.data(), 256 * 8);
         if (obj->hist_on_device) off_hist = add(nullptr, 256 * 4);
+        off_tab = add(nullptr, (size_t)kOtsuTabSize * 8);
     }
 
     apo_problem* P = new apo_problem();
@@ -299,6 +302,12 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
             }
         }
     }
+    if (e == cudaSuccess && kind == APO_OBJ_OTSU) {
+        e = launch_otsu_table(reinterpret_cast<const long long*>(base + off_p0),
+                              reinterpret_cast<const long long*>(base + off_p1),
+                              reinterpret_cast<double*>(base + off_tab), 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
     if (e != cudaSuccess) {
         cudaFree(P->mem);
         delete P;
@@ -319,6 +328,7 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
     if (kind == APO_OBJ_OTSU) {
         dp.P0 = reinterpret_cast<const long long*>(base + off_p0);
         dp.P1 = reinterpret_cast<const long long*>(base + off_p1);
+        dp.otsu_tab = reinterpret_cast<const double*>(base + off_tab);
     }
     *out = P;
     return APO_OK;
@@ -505,7 +515,9 @@ apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, b
         const RunSpec& s = specs_in[k];
         const int ps = s.prm.ps;
         const bool f64 = s.P->kind == APO_OBJ_OTSU;
-        cls[k] = {ps > kQueueMaxPs, f64, f64 ? 1 : qpl_of(s.P)};
+        // a lone run of a large population spreads over many CTAs
+        const bool grid = ps > kQueueMaxPs || (n == 1 && ps >= kGridSingleMinPs);
+        cls[k] = {grid, f64, f64 ? 1 : qpl_of(s.P)};
         if (cls[k].grid) {
             plans[k] = choose_plan(s.P, ps, false, true, kSmemMax);
         } else {

@@ -55,7 +55,15 @@ struct DevProblem {
     DevComp comp[kMaxComp];
     const long long* P0; // Otsu: prefix pixel counts [256]
     const long long* P1; // Otsu: prefix first moments [256]
+    const double* otsu_tab;  // Otsu: between-class term of every bin range [a, b]
 };
+
+// Packed index of the bin range [a, b] (0 <= a <= b <= 255) in the Otsu term table.
+__host__ __device__ __forceinline__ int otsu_tab_index(int a, int b)
+{
+    return 256 * a - (a * (a - 1)) / 2 + (b - a);
+}
+constexpr int kOtsuTabSize = 32896;   // 256 * 257 / 2
 
 // Shared-memory carve-up of one run (byte offsets into dynamic shared memory).
 struct SmemPlan {

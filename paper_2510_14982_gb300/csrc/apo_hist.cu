@@ -97,4 +97,36 @@ cudaError_t launch_otsu_prefix(const int32_t* d_hist, long long* d_P0, long long
     return cudaGetLastError();
 }
 
+// The between-class term omega_c (mu_c - mu_T)^2 of the class covering bins
+// [a, b], for every range: omega = n / N, mu = s / n, computed with explicit
+// round-to-nearest float64 operations in the order ((omega * dm) * dm); 0 for
+// an empty range.  Summing these terms in class order reproduces the
+// sigma_B^2 of Sec. 5.2's Otsu objective bit for bit.
+__global__ void otsu_table_kernel(const long long* __restrict__ P0, const long long* __restrict__ P1,
+                                  double* __restrict__ tab)
+{
+    const long long N = P0[255], S = P1[255];
+    const double muT = __ddiv_rn((double)S, (double)N);
+    for (int a = blockIdx.x; a < 256; a += gridDim.x) {
+        for (int b = a + threadIdx.x; b < 256; b += blockDim.x) {
+            const long long nc = P0[b] - (a > 0 ? P0[a - 1] : 0ll);
+            const long long sc = P1[b] - (a > 0 ? P1[a - 1] : 0ll);
+            double term = 0.0;
+            if (nc > 0) {
+                const double omega = __ddiv_rn((double)nc, (double)N);
+                const double mu = __ddiv_rn((double)sc, (double)nc);
+                const double dm = __dsub_rn(mu, muT);
+                term = __dmul_rn(__dmul_rn(omega, dm), dm);
+            }
+            tab[otsu_tab_index(a, b)] = term;
+        }
+    }
+}
+
+cudaError_t launch_otsu_table(const long long* d_P0, const long long* d_P1, double* d_tab, cudaStream_t st)
+{
+    otsu_table_kernel<<<256, 256, 0, st>>>(d_P0, d_P1, d_tab);
+    return cudaGetLastError();
+}
+
 }  // namespace apo

@@ -66,5 +66,6 @@ cudaError_t launch_histogram_u8(const uint8_t* d_px, int64_t n_per_image, int n_
                                 int32_t* d_hist, cudaStream_t st);
 cudaError_t launch_otsu_prefix(const int32_t* d_hist, long long* d_P0, long long* d_P1,
                                cudaStream_t st);
+cudaError_t launch_otsu_table(const long long* d_P0, const long long* d_P1, double* d_tab, cudaStream_t st);
 
 }  // namespace apo

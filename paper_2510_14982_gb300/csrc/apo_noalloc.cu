@@ -93,7 +93,7 @@ extern "C" apo_status apo_run_device_noalloc(const apo_problem* P, const apo_par
     const int ps = p->ps, T = p->max_iter, Dp = P->Dp;
     const bool fit64 = P->kind == APO_OBJ_OTSU;
     const int qpl = fit64 ? 1 : (P->D <= 64 ? 1 : (P->D <= 128 ? 2 : 4));
-    const bool grid = ps > kQueueMaxPsNA;
+    const bool grid = ps > kQueueMaxPsNA || ps >= 128;   // same rule as a lone apo_run_device
     SmemPlan plan = grid ? choose_plan(P, ps, false, true, kSmemMaxNA) : choose_plan(P, ps, true, false, kSmemMaxNA);
     if (!grid && plan.total > kSmemMaxNA) plan = choose_plan(P, ps, false, false, kSmemMaxNA);
     if (plan.total > kSmemMaxNA) return fail(APO_ERR_UNSUPPORTED, "problem needs too much shared memory");

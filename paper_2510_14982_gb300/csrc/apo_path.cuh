@@ -181,11 +181,11 @@ __device__ __forceinline__ float seg_value(const float* z, int zs, const DevComp
 }
 
 // Otsu between-class variance of one row by one warp (thresholds in lanes
-// 0..T-1), negated.  The float64 operations follow a fixed order with
-// explicit round-to-nearest intrinsics (no contraction) so that the value is
-// reproducible bit for bit.
-__device__ __forceinline__ double otsu_row(const float* x, int T, const long long* P0, const long long* P1,
-                           int* scratch)
+// 0..T-1), negated.  The thresholds are sorted by rank counting; lane c then
+// fetches the precomputed float64 term of class c (the bin range between
+// consecutive distinct thresholds), and lane 0 adds the terms in class order
+// with round-to-nearest adds, reproducing the class-by-class sum exactly.
+__device__ __forceinline__ double otsu_row(const float* x, int T, const double* __restrict__ tab, int* scratch)
 {
     const int lane = threadIdx.x & 31;
     int tv = 0;
@@ -202,30 +202,24 @@ __device__ __forceinline__ double otsu_row(const float* x, int T, const long lon
     __syncwarp();
     if (lane < T) scratch[rank] = tv;
     __syncwarp();
-    double sigma = 0.0;
-    if (lane == 0) {
-        const long long N = P0[255], Ssum = P1[255];
-        const double muT = __ddiv_rn((double)Ssum, (double)N);
-        int prev = -1;
-        for (int c = 0; c <= T; ++c) {
-            const int hi = (c < T) ? scratch[c] : 255;
-            long long nc = 0, sc = 0;
-            if (hi > prev) {
-                nc = P0[hi] - (prev >= 0 ? P0[prev] : 0ll);
-                sc = P1[hi] - (prev >= 0 ? P1[prev] : 0ll);
-                prev = hi;
-            }
-            if (nc > 0) {
-                const double omega = __ddiv_rn((double)nc, (double)N);
-                const double mu = __ddiv_rn((double)sc, (double)nc);
-                const double dm = __dsub_rn(mu, muT);
-                double term = __dmul_rn(omega, dm);
-                term = __dmul_rn(term, dm);
-                sigma = __dadd_rn(sigma, term);
-            }
+    // class c covers (t_{c-1}, t_c] with t_{-1} = -1, t_T = 255; a repeated
+    // threshold gives no class
+    double term = 0.0;
+    bool has = false;
+    if (lane <= T) {
+        const int hi = lane < T ? scratch[lane] : 255;
+        const int prev = lane > 0 ? scratch[lane - 1] : -1;
+        if (hi > prev) {
+            has = true;
+            term = tab[otsu_tab_index(prev + 1, hi)];
         }
     }
-    sigma = __shfl_sync(0xffffffffu, sigma, 0);
+    double sigma = 0.0;
+    for (int c = 0; c <= T; ++c) {
+        const double v = __shfl_sync(0xffffffffu, term, c);
+        const bool h = __shfl_sync(0xffffffffu, has, c);
+        if (h) sigma = __dadd_rn(sigma, v);
+    }
     __syncwarp();
     return -sigma;
 }
@@ -240,7 +234,7 @@ __device__ __forceinline__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (P.kind == kOtsu) {
         for (int row = warp; row < rows; row += nw) {
-            const double f = otsu_row(S.Xc + (size_t)row * Dp, D, S.P0, S.P1, S.otsu + warp * 32);
+            const double f = otsu_row(S.Xc + (size_t)row * Dp, D, P.otsu_tab, S.otsu + warp * 32);
             if (lane == 0) S.rowF[row] = (FitT)f;
         }
         __syncthreads();

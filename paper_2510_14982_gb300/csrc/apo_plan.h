@@ -20,7 +20,8 @@ inline int plan_pow2(int v)
 // Layout for a run of population ps (0 for the evaluation hooks).  grid
 // selects the cooperative-grid layout (512 threads, 64-row chunks);
 // otherwise the resident / work-queue layout (256 threads, 32-row chunks).
-inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool mt_smem, bool grid)
+inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool mt_smem, bool grid,
+                               int chunk = 0)
 {
     const bool fit64 = P->kind == 6;
     const size_t fsz = fit64 ? 8 : 4;
@@ -30,7 +31,7 @@ inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool
     L.ps_pad = ps > 0 ? plan_pow2(ps) : 0;
     L.resident = resident;
     L.mt_smem = mt_smem;
-    L.chunk = grid ? kGridChunk : kChunk;
+    L.chunk = chunk > 0 ? chunk : (grid ? kGridChunk : kChunk);
     L.threads = grid ? kGridThreads : kThreads;
     const size_t ch = (size_t)L.chunk;
     size_t off = 0;
@@ -77,7 +78,9 @@ inline SmemPlan choose_plan(const apo_problem* P, int ps, bool resident, bool gr
         SmemPlan L = make_smem_plan(P, ps, resident, true, grid);
         if (L.total <= smem_max) return L;
     }
-    return make_smem_plan(P, ps, resident, false, grid);
+    SmemPlan L = make_smem_plan(P, ps, resident, false, grid);
+    if (grid && L.total > smem_max) L = make_smem_plan(P, ps, resident, false, grid, kChunk);   // 32-row chunks
+    return L;
 }
 
 }  // namespace apo

@@ -49,15 +49,19 @@ __global__ void to_bf16_kernel(int n, int D, int Kp, const float* __restrict__ x
 
 // idx[i] = uniform index in [0, n) from Philox (seed, step, i); the whole
 // set in order when the batch covers it (B >= n).
-__global__ void rand_idx_kernel(int B, int n, uint32_t seed, uint32_t step, int* __restrict__ idx)
+// Rows are taken from the window [start, start + n) of a ring buffer of cap rows.
+__global__ void rand_idx_kernel(int B, int n, uint32_t seed, uint32_t step, int* __restrict__ idx, long long start,
+                                int cap)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = 0;
     if (i < B && B >= n) {
-        idx[i] = i < n ? i : n - 1;
+        j = i < n ? i : n - 1;
     } else if (i < B) {
         const uint4 w = philox(step, (uint32_t)i, 0xFFFFFFFFu, 0x100u, seed, 0x7FFFFFFFu);
-        idx[i] = (int)idx_draw(w.x, (uint32_t)n);
+        j = (int)idx_draw(w.x, (uint32_t)n);
     }
+    if (i < B) idx[i] = (int)((start + j) % cap);
 }
 
 }  // namespace
@@ -302,12 +306,13 @@ namespace {
 // `steps` Adam steps on batches of `batch` rows drawn uniformly from the
 // first n rows of (Xa bf16 [.][Kp], ta).
 apo_status mlp_train_rows(apo_mlp* M, const __nv_bfloat16* Xa, const float* ta, int n, int steps, int batch, float lr,
-                          uint32_t seed, cudaStream_t st)
+                          uint32_t seed, cudaStream_t st, long long start = 0, int cap = 0)
 {
+    if (cap <= 0) cap = n;
     batch = std::min(batch, M->cap);
     if (batch >= n) batch = n;   // full batch, rows in order
     for (int s = 0; s < steps; ++s) {
-        rand_idx_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, n, seed, (uint32_t)(M->step + 1), M->idx);
+        rand_idx_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, n, seed, (uint32_t)(M->step + 1), M->idx, start, cap);
         SUR_CUDA(cudaGetLastError());
         SUR_CUDA(launch_gather_rows(batch, M->Kp, M->idx, Xa, ta, M->Xb, M->t, st));
         apo_status rc = mlp_forward_rows(M, batch, st);
@@ -508,12 +513,16 @@ __global__ void __launch_bounds__(kSurThreads) surr_select_kernel(
 }
 
 // Training targets: standardised log1p(F - min F) over the archive.
-__global__ void __launch_bounds__(1024) surr_targets_kernel(int n, const float* __restrict__ Fa, float* __restrict__ tgt)
+__global__ void __launch_bounds__(1024) surr_targets_kernel(int n, const float* __restrict__ Fa_ring,
+                                                            float* __restrict__ tgt_ring, long long start, int cap)
 {
+    // rows i of the window live at (start + i) mod cap
+#define Fa(i) Fa_ring[(start + (i)) % cap]
+#define TG(i) tgt_ring[(start + (i)) % cap]
     __shared__ double red[1024];
     __shared__ double s_min, s_mean, s_std;
     double mn = INFINITY;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) mn = fmin(mn, (double)Fa[i]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) mn = fmin(mn, (double)Fa(i));
     red[threadIdx.x] = mn;
     __syncthreads();
     for (int o = blockDim.x / 2; o; o >>= 1) {
@@ -524,7 +533,7 @@ __global__ void __launch_bounds__(1024) surr_targets_kernel(int n, const float* 
     __syncthreads();
     double s = 0.0, s2 = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double v = log1p((double)Fa[i] - s_min);
+        const double v = log1p((double)Fa(i) - s_min);
         s += v;
         s2 += v * v;
     }
@@ -545,7 +554,9 @@ __global__ void __launch_bounds__(1024) surr_targets_kernel(int n, const float* 
     if (threadIdx.x == 0) s_std = sqrt(fmax(red[0] / n - s_mean * s_mean, 1e-12));
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x)
-        tgt[i] = (float)((log1p((double)Fa[i] - s_min) - s_mean) / s_std);
+        TG(i) = (float)((log1p((double)Fa(i) - s_min) - s_mean) / s_std);
+#undef Fa
+#undef TG
 }
 
 double spearman(const std::vector<float>& a, const std::vector<float>& b)
@@ -760,10 +771,14 @@ extern "C" apo_status apo_run_surrogate(const apo_problem* P, const apo_params* 
                 cudaStreamSynchronize(st);
                 S.last_rank_corr = spearman(hp, ht);
             }
-            const int n = (int)std::min<long long>(arch_count, acap);
-            surr_targets_kernel<<<1, 1024, 0, st>>>(n, Fa, tgt);
+            // the training window: the most recent rows of the archive
+            const long long avail = std::min<long long>(arch_count, acap);
+            const int n = (int)std::min<long long>(avail, sp->train_window > 0 ? sp->train_window : avail);
+            const long long start = ((arch_count - n) % acap + acap) % acap;
+            surr_targets_kernel<<<1, 1024, 0, st>>>(n, Fa, tgt, start, acap);
             cudaEventRecord(tr0, st);
-            rc = mlp_train_rows(M, Xa, tgt, n, sp->train_steps, sp->batch, sp->lr, sp->net_seed + (uint32_t)t, st);
+            rc = mlp_train_rows(M, Xa, tgt, n, sp->train_steps, sp->batch, sp->lr, sp->net_seed + (uint32_t)t, st,
+                                start, acap);
             cudaEventRecord(tr1, st);
             if (rc != APO_OK) return fail(rc, nullptr);
             ++S.retrains;
@@ -773,9 +788,8 @@ extern "C" apo_status apo_run_surrogate(const apo_problem* P, const apo_params* 
             float ms = 0.f;
             cudaEventElapsedTime(&ms, tr0, tr1);
             train_ms += ms;
-        } else if (!screening && S.retrains > 0) {
-            ++S.fallback_iters;
         }
+        if (kk == 1 && t > R_every) ++S.fallback_iters;
     }
     // the best of the final population
     surr_sort_kernel<<<1, 1024, sort_smem, st>>>(ps, ps_pad, F[cur], pm[pc], pm[pc ^ 1], d_curve, T + 1);
