@@ -10,16 +10,20 @@
 
 namespace apo {
 
-constexpr int kHistThreads = 512;
+constexpr int kHistThreads = 256;
 constexpr int kHistWarps = kHistThreads / 32;
+constexpr int kHistCopies = 4;                 // sub-histograms per warp (lane & 3)
+constexpr int kHistStride = 257;               // one pad word: copies sit on shifted banks
 
 __global__ void __launch_bounds__(kHistThreads) histogram_u8_kernel(const uint8_t* __restrict__ px,
                                                                     long long n_per_image,
                                                                     long long chunk, int32_t* hist)
 {
-    __shared__ unsigned sub[kHistWarps][256];
-    const int tid = threadIdx.x, warp = tid >> 5;
-    for (int i = tid; i < kHistWarps * 256; i += kHistThreads) (&sub[0][0])[i] = 0;
+    // Equal pixel values within a warp serialise shared-memory atomics; four
+    // copies per warp (lanes split by lane & 3) cut those collisions.
+    __shared__ unsigned sub[kHistWarps * kHistCopies * kHistStride];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < kHistWarps * kHistCopies * kHistStride; i += kHistThreads) sub[i] = 0;
     __syncthreads();
 
     const int image = blockIdx.y;
@@ -27,7 +31,7 @@ __global__ void __launch_bounds__(kHistThreads) histogram_u8_kernel(const uint8_
     long long end = begin + chunk;
     if (end > n_per_image) end = n_per_image;
     const uint8_t* base = px + (size_t)image * (size_t)n_per_image;
-    unsigned* h = sub[warp];
+    unsigned* h = sub + (warp * kHistCopies + (lane & (kHistCopies - 1))) * kHistStride;
 
     // bytes before the first 16-byte boundary and after the last one
     const uintptr_t addr = reinterpret_cast<uintptr_t>(base + begin);
@@ -37,7 +41,20 @@ __global__ void __launch_bounds__(kHistThreads) histogram_u8_kernel(const uint8_
     const long long vbeg = begin + head;
     const long long nvec = (end - vbeg) >> 4;
     const uint4* v = reinterpret_cast<const uint4*>(base + vbeg);
-    for (long long i = tid; i < nvec; i += kHistThreads) {
+    long long i = tid;
+    for (; i + kHistThreads < nvec; i += 2 * kHistThreads) {   // two 16-byte loads in flight
+        const uint4 w0 = __ldcs(v + i);
+        const uint4 w1 = __ldcs(v + i + kHistThreads);
+        const uint32_t words[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            atomicAdd(&h[words[k] & 255u], 1u);
+            atomicAdd(&h[(words[k] >> 8) & 255u], 1u);
+            atomicAdd(&h[(words[k] >> 16) & 255u], 1u);
+            atomicAdd(&h[words[k] >> 24], 1u);
+        }
+    }
+    for (; i < nvec; i += kHistThreads) {
         const uint4 w = __ldcs(v + i);
         const uint32_t words[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -48,12 +65,12 @@ __global__ void __launch_bounds__(kHistThreads) histogram_u8_kernel(const uint8_
             atomicAdd(&h[words[k] >> 24], 1u);
         }
     }
-    for (long long i = vbeg + (nvec << 4) + tid; i < end; i += kHistThreads) atomicAdd(&h[base[i]], 1u);
+    for (long long j = vbeg + (nvec << 4) + tid; j < end; j += kHistThreads) atomicAdd(&h[base[j]], 1u);
     __syncthreads();
     for (int b = tid; b < 256; b += kHistThreads) {
         unsigned s = 0;
 #pragma unroll
-        for (int w = 0; w < kHistWarps; ++w) s += sub[w][b];
+        for (int c = 0; c < kHistWarps * kHistCopies; ++c) s += sub[c * kHistStride + b];
         if (s) atomicAdd(reinterpret_cast<unsigned*>(hist + (size_t)image * 256 + b), s);
     }
 }
@@ -66,9 +83,9 @@ cudaError_t launch_histogram_u8(const uint8_t* d_px, int64_t n_per_image, int n_
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // about four CTAs per SM over the whole batch, each a 16-byte multiple
+    // about eight CTAs per SM over the whole batch, each a 16-byte multiple
     long long total = n_per_image * (long long)n_images;
-    long long chunk = total / ((long long)sms * 4);
+    long long chunk = total / ((long long)sms * 8);
     if (chunk < 65536) chunk = 65536;
     chunk = (chunk + 15) & ~15ll;
     long long per_image = (n_per_image + chunk - 1) / chunk;
