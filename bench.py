@@ -107,11 +107,51 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus=None):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def replica_setup(backend="nccl"):
+    """(world, rank, local rank) from the torchrun environment; with more than
+    one rank, joins the process group.  Every rank runs its own replica of the
+    workload (the runs share nothing), so the group carries only the timing
+    barriers and the max over ranks."""
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+    return world, rank, local
+
+
+def sync_ranks(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """The maximum of x over all ranks (the slowest replica sets the time)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(step, rank):
+    """Seed of a replica's runs in a step: distinct for every (step, rank) below 100 ranks."""
+    return 100 * step + rank
+
+
+def aggregate_rate(world, units_per_rank, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
 
 
 def cpu_oracle_sample(specs, ps, T_sample, n_threads):
@@ -163,11 +203,8 @@ def run_batched(args):
     work-queue launch replayed from a CUDA graph; beside it the same kind of
     runs launched one at a time (a bounded sample, scaled)."""
     import torch
-    world, rank, local = dist_setup(args.gpus)
+    world, rank, local = replica_setup()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
     from paper_2510_14982_gb300 import apo
     T = args.iters or 1000
     runs = inputs.batched_runs(args.runs, seed=rank)
@@ -192,8 +229,7 @@ def run_batched(args):
     for _ in range(args.warmup):
         graph.replay()
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    sync_ranks(world)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     ms = []
@@ -206,12 +242,9 @@ def run_batched(args):
             e1.record()
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * updates / (total_ms * 1e-3)
+    total_ms = max_over_ranks(sum(ms), world, dev)
+    sync_ranks(world)
+    value = aggregate_rate(world, args.steps * updates, total_ms * 1e-3)
     # the same kind of runs launched one at a time (one apo_run_device call each)
     k_s = min(args.per_run_sample, n)
     sx = torch.zeros(50, device=dev)
@@ -269,7 +302,7 @@ def run_thresholding(args):
     image, 1024 runs in one autotuned persistent launch.  One step = the
     histograms of all images and the 1024 runs."""
     import torch
-    world, rank, local = dist_setup(args.gpus)
+    world, rank, local = replica_setup()
     torch.cuda.set_device(local)
     from paper_2510_14982_gb300 import apo
     dev = torch.device("cuda", local)
@@ -302,6 +335,7 @@ def run_thresholding(args):
         apo.apo_histogram_u8(imgs, npx, n_img, hist)
         graph.replay()
     torch.cuda.synchronize()
+    sync_ranks(world)
     hist_ms, apo_ms = [], []
     with Clocks(local) as clk:
         for _ in range(args.steps):
@@ -314,7 +348,8 @@ def run_thresholding(args):
             torch.cuda.synchronize()
             hist_ms.append(ev[0].elapsed_time(ev[1]))
             apo_ms.append(ev[1].elapsed_time(ev[2]))
-    total_ms = sum(hist_ms) + sum(apo_ms)
+    total_ms = max_over_ranks(sum(hist_ms) + sum(apo_ms), world, dev)
+    sync_ranks(world)
     updates = n * 100 * T
     pk = peaks()
     hbm = float(pk.get("hbm_gbs", 6800.0))
@@ -323,7 +358,7 @@ def run_thresholding(args):
     ref = torch.bincount(imgs[0].long(), minlength=256).to(torch.int32)
     exact = bool(torch.equal(ref, hist[0]))
     line = {
-        "metric": "APO candidate updates/s", "value": world * args.steps * updates / (total_ms * 1e-3),
+        "metric": "APO candidate updates/s", "value": aggregate_rate(world, args.steps * updates, total_ms * 1e-3),
         "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u8 histogram, f64 Otsu fitness, f32 positions", "data": "synthetic",
@@ -348,7 +383,7 @@ def run_surrogate(args):
     method's median best (over --seeds seeds), in iterations, true evaluations
     and wall time."""
     import torch
-    world, rank, local = dist_setup(args.gpus)
+    world, rank, local = replica_setup()
     torch.cuda.set_device(local)
     from paper_2510_14982_gb300 import apo
     T = args.iters or 300
@@ -375,10 +410,14 @@ def run_surrogate(args):
     P = [plain(s) for s in range(args.seeds)]
     target = float(np.median([p[0] for p in P]))
     S = []
+    torch.cuda.synchronize()
+    sync_ranks(world)
     with Clocks(local) as clk:
         for s in range(max(args.steps, args.seeds)):
             S.append(surr(s))
     times = [x[2] for x in S[:args.steps]]
+    t_max = max_over_ranks(sum(times), world, torch.device("cuda", local))
+    sync_ranks(world)
     stt = S[0][3]
 
     def iters_to(curve):
@@ -396,14 +435,14 @@ def run_surrogate(args):
     s_t, s_it = med_time_to(S[:args.seeds])
     screened = stt["screened"]
     line = {
-        "metric": "APO candidate updates/s", "value": world * screened * len(times) / sum(times), "unit": "updates/s",
+        "metric": "APO candidate updates/s", "value": aggregate_rate(world, screened * len(times), t_max), "unit": "updates/s",
         "n_gpus": world, "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 APO, bf16 MLP (fp32 accumulate)",
         "data": "synthetic",
         "config": {"workload": "surrogate-assisted APO: composition of 10 (D 200), ps 256, %d iterations, k 8, retrain "
                                "every 10 on the last 1280 evaluations (50 Adam steps of 512)" % T,
                    "l2": "working set resident (no flush)"},
-        "true_evals_per_s": world * stt["true_evals"] * len(times) / sum(times),
+        "true_evals_per_s": aggregate_rate(world, stt["true_evals"] * len(times), t_max),
         "time_to_target": {"target_best_f": target, "target": "median best of plain APO over %d seeds" % args.seeds,
                            "surrogate_s": s_t, "plain_s": p_t, "ratio": s_t / p_t if p_t > 0 else None,
                            "surrogate_iters": s_it, "plain_iters": p_it,
@@ -433,7 +472,9 @@ def main():
     ap.add_argument("--runs", type=int, default=1024, help="batched workload: number of runs")
     ap.add_argument("--per-run-sample", type=int, default=24, help="batched: runs timed with one launch each")
     ap.add_argument("--iters", type=int, default=0, help="override the iteration count (profiling)")
-    ap.add_argument("--ref-iters", type=int, default=40, help="oracle iterations per timed sample")
+    ap.add_argument("--ref-iters", type=int, default=40, help="oracle iterations per --impl reference step")
+    ap.add_argument("--cpu-baseline-iters", type=int, default=200,
+                    help="oracle iterations of the cpu_baseline sample (about 10 s of CPU work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -447,11 +488,8 @@ def main():
         return run_surrogate(args)
 
     import torch
-    world, rank, local = dist_setup(args.gpus)
+    world, rank, local = replica_setup()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
     from paper_2510_14982_gb300 import apo
 
     specs, ps, T, label = workload(args.workload, args.iters)
@@ -469,14 +507,13 @@ def main():
     ev_run1.record()
 
     def step(k):
-        prms = [apo.apo_params_make(ps, 1, 0.1, T, 100 * k + rank, j) for j in range(n)]
+        prms = [apo.apo_params_make(ps, 1, 0.1, T, replica_seed(k, rank), j) for j in range(n)]
         apo.apo_run_batch(probs, prms, bx, Dmax, bf, cv, T + 1)
 
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    sync_ranks(world)
     apo.apo_set_timing_events(ev_run0, ev_run1)
     step_ms, run_ms = [], []
     e0 = torch.cuda.Event(enable_timing=True)
@@ -492,15 +529,11 @@ def main():
             step_ms.append(e0.elapsed_time(e1))
             run_ms.append(ev_run0.elapsed_time(ev_run1))
     apo.apo_set_timing_events(None, None)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    sync_ranks(world)
     updates = world * args.steps * n * ps * T
     evals = world * args.steps * n * ps * (T + 1)
-    value = updates / (total_ms * 1e-3)
+    value = aggregate_rate(world, args.steps * n * ps * T, total_ms * 1e-3)
 
     # end to end through the public API: problem upload from host memory,
     # the batch call, and the results read back into pinned host memory
@@ -547,7 +580,8 @@ def main():
         "true_evals_per_s": evals / (total_ms * 1e-3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": None,
-                     "kernel": "run_kernel (FP32 FMA rotation, 2 D^2 flop per evaluation)",
+                     "kernel": "%s (FP32 FMA rotation, 2 D^2 flop per evaluation)" % (
+                         "grid_kernel" if ps > 1024 or (n == 1 and ps >= 128) else "run_kernel"),
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s clock)" % (
                          float(pk.get("sm_max_mhz", 2070.0)), pk["source"]),
                      "kernel_ms": statistics.mean(run_ms)},
@@ -556,9 +590,9 @@ def main():
         "e2e": e2e,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, thr = cpu_oracle_sample(specs, ps, args.ref_iters, os.cpu_count() or 1)
+        v, dt, thr = cpu_oracle_sample(specs, ps, args.cpu_baseline_iters, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": thr, "kind": "oracle",
-                                "sample": "%d forms x ps %d x %d iterations (%.1f s)" % (n, ps, args.ref_iters, dt)}
+                                "sample": "%d forms x ps %d x %d iterations (%.1f s)" % (n, ps, args.cpu_baseline_iters, dt)}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
