@@ -56,6 +56,8 @@ constexpr int kQueueMaxPs = 1024;
 constexpr int kGridMinRows = 8;
 // A run launched alone uses the grid kernel from this population size on.
 constexpr int kGridSingleMinPs = 128;
+// barrier words of different runs on different L2 lines (their CTAs poll them)
+constexpr size_t kBarStride = 256;
 
 // Optional timing events around the iteration-loop kernels.
 cudaEvent_t g_ev_before = nullptr, g_ev_after = nullptr;
@@ -481,7 +483,7 @@ struct Prepared {
     ApoRun* d_runs = nullptr;   // launch-ordered descriptors
     int* d_offs = nullptr;
     int* d_ctrl = nullptr;      // queue counters (one per launch)
-    unsigned char* d_bars = nullptr;  // barrier words, 16 bytes per run
+    unsigned char* d_bars = nullptr;  // barrier words, one 256-byte line per run
     int n = 0, n_work = 0, max_ps_pad = 1;
     std::vector<LaunchInfo> launches;
     std::vector<RunSpec> order;           // specs in launch order
@@ -577,7 +579,7 @@ apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, b
     const size_t off_runs = take(sizeof(ApoRun) * n);
     const size_t off_offs = take(sizeof(int) * (n + 1));
     const size_t off_ctrl = take(sizeof(int) * std::max<size_t>(PR.launches.size(), 1));
-    const size_t off_bars = take(16 * (size_t)n);
+    const size_t off_bars = take(kBarStride * (size_t)n);
     std::vector<size_t> off_dr(n), off_x0(n), off_x1(n), off_f0(n), off_f1(n), off_pg(n), off_kg(n);
     std::vector<int> offs(n + 1, 0);
     for (int i = 0; i < n; ++i) {
@@ -643,7 +645,7 @@ apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, b
         R.X_out = s.X_in;
         R.F_out = s.F_in;
         R.best_x = s.best_x; R.best_f = s.best_f; R.curve = s.curve;
-        R.bar = reinterpret_cast<unsigned*>(PR.d_bars + 16 * (size_t)i);
+        R.bar = reinterpret_cast<unsigned*>(PR.d_bars + kBarStride * (size_t)i);
         if (cls[k].grid) {
             R.perm_g = reinterpret_cast<uint32_t*>(base + off_pg[i]);
             R.keys_g = base + off_kg[i];
@@ -679,7 +681,7 @@ apo_status launch_prepared(const Prepared& PR, cudaStream_t st)
     if (!status) { set_err("status word allocation failed"); return APO_ERR_OOM; }
     unsigned char* base = static_cast<unsigned char*>(PR.ws);
     APO_CUDA(cudaMemsetAsync(PR.d_ctrl, 0, sizeof(int) * std::max<size_t>(PR.launches.size(), 1), st));
-    APO_CUDA(cudaMemsetAsync(PR.d_bars, 0, 16 * (size_t)PR.n, st));
+    APO_CUDA(cudaMemsetAsync(PR.d_bars, 0, kBarStride * (size_t)PR.n, st));
     for (int i = 0; i < PR.n; ++i) {
         const RunSpec& s = PR.order[i];
         if (!(s.flags & kFlagStepOut)) continue;

@@ -29,6 +29,11 @@ constexpr uint32_t kSlotPair = 6;   // per (rank, pair): k-, k+
 constexpr uint32_t kSlotDim = 7;    // per (rank, dim pair): Rand_d, mask key
 constexpr uint32_t kAll = 0xFFFFFFFFu;
 
+// Rank -> slot permutation entries of the grid kernel carry, in the top bit,
+// which of the two population buffers holds the slot's current row.
+constexpr uint32_t kLocBit = 0x80000000u;
+constexpr uint32_t kSlotMask = 0x7FFFFFFFu;
+
 enum Mode : int { kDormancy = 0, kReproduction = 1, kAutotrophic = 2, kHeterotrophic = 3 };
 enum Kind : int { kSphere = 0, kElliptic = 1, kRosenbrock = 2, kRastrigin = 3, kHybrid = 4,
                   kComposition = 5, kOtsu = 6 };
@@ -73,7 +78,7 @@ struct SmemPlan {
     int chunk;           // candidate rows evaluated together
     int threads;         // CTA size the plan was made for
     uint32_t X0, X1, F0, F1, perm0, perm1, keys, MT, o, lb, ub, ew, Xc, Xo, Yc, Zc,
-        rowF, compG, compA, P0, P1, otsu, red, seg, total;
+        rowF, compG, compA, P0, P1, otsu, red, nloc, total;
 };
 
 struct ApoRun {
@@ -249,6 +254,43 @@ __device__ uint32_t warp_kselect(const uint32_t (&key)[2 * QPL], uint32_t valid,
     return sel;
 }
 
+// The same subset as warp_kselect, found by interpolation: a threshold T with
+// exactly k valid keys below it selects the k smallest (every key below T is
+// smaller than every key at or above it, so index tie-breaks cannot arise).
+// The keys are uniform 32-bit Philox words, so interpolating between the
+// bracketing counts usually lands between the k-th and (k+1)-th smallest key
+// within a few warp-wide counts (about 3.2 on average for D in 10..200).  A
+// boundary tie, or no hit within ten counts (about 0.3% of selections),
+// falls back to the bitwise descent.  n = number of valid slots.
+template <int QPL>
+__device__ uint32_t warp_kselect_interp(const uint32_t (&key)[2 * QPL], uint32_t valid, int k, int n)
+{
+    if (k <= 0) return 0;
+    if (k >= n) return valid;
+    // invariant: clo = #(keys < lo) < k < chi = #(keys < hi)
+    unsigned long long lo = 0ull, hi = 1ull << 32;
+    int clo = 0, chi = n;
+#pragma unroll 1
+    for (int it = 0; it < 10 && hi - lo >= 2ull; ++it) {
+        // the boundary between the (k-clo)-th and (k-clo+1)-th of the chi-clo
+        // keys in [lo, hi) sits near the fraction (k - clo + 1/2) / (chi - clo + 1)
+        const float frac = ((float)(k - clo) + 0.5f) / (float)(chi - clo + 1);
+        unsigned long long T = lo + __float2ull_rz((float)(hi - lo) * frac);
+        if (T <= lo) T = lo + 1ull;
+        if (T >= hi) T = hi - 1ull;
+        const uint32_t t32 = (uint32_t)T;
+        uint32_t below = 0;
+#pragma unroll
+        for (int e = 0; e < 2 * QPL; ++e)
+            if (((valid >> e) & 1u) && key[e] < t32) below |= 1u << e;
+        const int c = __reduce_add_sync(0xffffffffu, __popc(below));
+        if (c == k) return below;
+        if (c < k) { lo = T; clo = c; }
+        else { hi = T; chi = c; }
+    }
+    return warp_kselect<QPL>(key, valid, k);
+}
+
 // ----------------------------------------------------------- barriers
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -272,37 +314,45 @@ __device__ __forceinline__ void set_status(int* status, int code)
 
 constexpr unsigned long long kBarrierTimeoutNs = 4000000000ull;  // 4 s per wait
 
-// Barrier over the g CTAs of one run.  Returns false (for every thread of the
-// CTA) when the run was aborted or the wait timed out; the caller then stops
-// the run.  `gen` is the CTA's count of barriers passed.
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+
+// Barrier over the g CTAs of one run.  bar[0] counts arrivals and is never
+// reset: the CTA's n-th barrier (n = ++gen) is passed once the count reaches
+// n g.  After the CTA-wide __syncthreads, thread 0 arrives with one release
+// reduction (cumulative over the CTA's writes) and polls with acquire loads,
+// so a barrier costs one trip to L2 plus the polling delay.  bar[2] is the
+// run's abort flag: every 64 polls the waiter checks it and the 4 s limit; a
+// wait that runs out sets APO_ERR_TIMEOUT and the flag.  Returns false (for
+// every thread of the CTA) when the run was aborted or the wait timed out;
+// the caller then stops the run.
 __device__ __noinline__ static bool run_barrier(unsigned* bar, int g, unsigned& gen, int* status, int* s_flag)
 {
     __syncthreads();
     if (g > 1) {
         if (threadIdx.x == 0) {
             int ok = 1;
-            __threadfence();
-            const unsigned arrived = atomicAdd(&bar[0], 1u);
-            if (arrived == (unsigned)g - 1u) {
-                atomicExch(&bar[0], 0u);
-                __threadfence();
-                atomicAdd(&bar[1], 1u);
-            } else {
-                const unsigned long long t0 = global_ns();
-                while (ld_acquire(&bar[1]) == gen) {
+            ++gen;
+            const unsigned target = gen * (unsigned)g;
+            red_release_add(&bar[0], 1u);
+            unsigned long long t0 = 0ull;
+            for (unsigned n = 1;; ++n) {
+                if ((int)(ld_acquire(&bar[0]) - target) >= 0) break;
+                if ((n & 63u) == 0u) {
                     if (ld_acquire(&bar[2]) != 0u) { ok = 0; break; }
-                    if (global_ns() - t0 > kBarrierTimeoutNs) {
+                    const unsigned long long now = global_ns();
+                    if (t0 == 0ull) {
+                        t0 = now;
+                    } else if (now - t0 > kBarrierTimeoutNs) {
                         set_status(status, 4 /* APO_ERR_TIMEOUT */);
                         atomicExch(&bar[2], 1u);
                         ok = 0;
                         break;
                     }
-                    __nanosleep(64);
                 }
             }
-            if (ld_acquire(&bar[2]) != 0u) ok = 0;
-            ++gen;
-            __threadfence();
             *s_flag = ok;
         }
         __syncthreads();

@@ -222,7 +222,7 @@ __device__ __forceinline__ void run_one(const ApoRun& R, int local, unsigned cha
         for (int c0 = r0; c0 < r1; c0 += CH) {
             const int rows = min(CH, r1 - c0);
             for (int row = warp; row < rows; row += nw)
-                gen_step_row<FitT, QPL>(R, S, Xs[cur], Fs[cur], perm, res, t, c0 + row, row);
+                gen_step_row<FitT, QPL>(R, S, Xs[cur], nullptr, Fs[cur], perm, res, true, t, c0 + row, row);
             __syncthreads();
             eval_chunk<FitT>(R, S, rows);
             // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i).
@@ -294,15 +294,22 @@ __global__ void __launch_bounds__(kThreads, 2) run_kernel(const ApoRun* __restri
 
 // ------------------------------------------------------------ grid mode
 // g CTAs run one optimisation run; CTA `local` owns the rank positions
-// [r0, r1) of every iteration and keeps a full copy of the rank -> slot
-// permutation in shared memory.  Per iteration:
-//   R1  sort the keys (F, previous rank) of the own rank range and publish
+// local, local + g, local + 2 g, ... of every iteration and keeps a full copy
+// of the rank -> slot permutation in shared memory.  Per iteration:
+//   R1  sort the keys (F, previous rank) of the own positions and publish
 //       them as a sorted segment of keys_g;                       barrier A
-//   R2  the new rank of each own key = its position in its own segment plus
-//       its lower bound in every other segment (the stable sort of
-//       Algorithm 1, distributed); scatter perm_g[rank] = slot;    barrier B
-//   R3  copy perm_g, then generate, evaluate and replace the own rank range;
-//       candidates read the double-buffered snapshot of the iteration.
+//   R2  the new rank of each own key = its position among the own keys plus
+//       the number of other segments' keys below it (the stable sort of
+//       Algorithm 1, distributed).  Every other key is located among the
+//       own sorted keys by binary search and counted there; a prefix sum
+//       of the counts gives the ranks; scatter perm_g[rank] = slot.  barrier B
+//   R3  copy perm_g (its head is the best of the population, the curve
+//       value), then generate, evaluate and replace the own positions.
+//       Each slot's current row lives in one of two buffers, named by the
+//       top bit of its perm entry; an accepted candidate is written to the
+//       other buffer, so the iteration's readers keep seeing the snapshot
+//       and rejected rows are never copied.  One more R1/R2 after the last
+//       iteration ranks the final population for the best.
 __device__ __forceinline__ unsigned long long lds_key(uint32_t a, unsigned long long*)
 {
     unsigned long long v;
@@ -332,15 +339,6 @@ __device__ __forceinline__ int lower_bound_key(const typename KeyOf<FitT>::T* se
     return lo;
 }
 
-__device__ __forceinline__ unsigned long long shfl_xor_key(unsigned long long v, int m)
-{
-    return __shfl_xor_sync(0xffffffffu, v, m);
-}
-__device__ __forceinline__ ulonglong2 shfl_xor_key(ulonglong2 v, int m)
-{
-    return make_ulonglong2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
-}
-
 // Copies n elements from global (L2, bypassing L1) to shared memory with
 // eight independent loads in flight per thread.
 template <typename T>
@@ -361,6 +359,36 @@ __device__ __forceinline__ void copy_cg(T* dst, const T* __restrict__ src, int n
     }
 }
 
+// Inclusive prefix sums of a[0, n) in place, by all threads of the CTA; each
+// warp scans a contiguous range, offset by the totals of the warps before it
+// (wsum: one int per warp).
+__device__ __forceinline__ void block_scan_inclusive(int* a, int n, int* wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int per = (n + nw - 1) / nw;
+    const int b = min(n, warp * per), e = min(n, b + per);
+    int carry = 0;
+    for (int base = b; base < e; base += 32) {
+        const int i = base + lane;
+        int v = i < e ? a[i] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        v += carry;
+        if (i < e) a[i] = v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (lane == 0) wsum[warp] = carry;
+    __syncthreads();
+    int off = 0;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    if (off)
+        for (int i = b + lane; i < e; i += 32) a[i] += off;
+    __syncthreads();
+}
+
 template <typename FitT, int QPL>
 __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned char* smem, int* status, int* s_flag)
 {
@@ -379,28 +407,36 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
     float* Xs[2] = {R.X[0], R.X[1]};
     FitT* Fs[2] = {static_cast<FitT*>(R.F[0]), static_cast<FitT*>(R.F[1])};
     uint32_t* perm = S.perm[0];
-    KT* keys = static_cast<KT*>(S.keys);
+    KT* keys = static_cast<KT*>(S.keys);      // own keys in the current rank order
     KT* keys_g = static_cast<KT*>(R.keys_g);
-    int* seg = S.seg;   // seg[c] = first rank position of CTA c; seg[g] = ps
-    for (int c = tid; c <= g; c += NT) seg[c] = (int)((long long)ps * c / g);
-    const int r0 = (int)((long long)ps * local / g);
-    const int r1 = (int)((long long)ps * (local + 1) / g);
-    const int nown = r1 - r0;
+    // own rank positions: local, local + g, local + 2 g, ... (interleaved, so
+    // that every CTA gets the same mix of ranks and modes); their keys take
+    // the segment [kb, kb + nown) of keys_g
+    const int nown = (ps - local + g - 1) / g;
+    const int kb = local * (ps / g) + min(local, ps % g);
+    auto pos_of = [&](int m) { return local + g * m; };
     int npad = 1;
     while (npad < nown) npad <<= 1;
+    // own keys sorted: a second array when they are ranked by counting (with
+    // g >= 2 two padded own ranges fit the ps_pad keys of the plan), else
+    // sorted in place
+    const bool count_rank = nown <= 2 * NT && g >= 2;
+    KT* skeys = count_rank ? keys + npad : keys;
+    int* hist = reinterpret_cast<int*>(S.perm[1]);   // [nown]: other keys per own position
     for (int r = tid; r < ps; r += NT) perm[r] = (uint32_t)r;
     __syncthreads();
 
     if (R.flags & kFlagInit) {
-        for (int c0 = r0; c0 < r1; c0 += CH) {
-            const int rows = min(CH, r1 - c0);
-            for (int row = warp; row < rows; row += nw) gen_init_row<FitT, QPL>(R, S, c0 + row, row);
+        for (int c0 = 0; c0 < nown; c0 += CH) {
+            const int rows = min(CH, nown - c0);
+            for (int row = warp; row < rows; row += nw) gen_init_row<FitT, QPL>(R, S, pos_of(c0 + row), row);
             __syncthreads();
             eval_chunk<FitT>(R, S, rows);
             for (int row = warp; row < rows; row += nw) {
-                float* dst = Xs[0] + (size_t)(c0 + row) * Dp;
+                const int p = pos_of(c0 + row);
+                float* dst = Xs[0] + (size_t)p * Dp;
                 for (int d = lane; d < Dp; d += 32) dst[d] = S.Xc[(size_t)row * Dp + d];
-                if (lane == 0) Fs[0][c0 + row] = S.rowF[row];
+                if (lane == 0) Fs[0][p] = S.rowF[row];
             }
             __syncthreads();
         }
@@ -409,94 +445,116 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
     int cur = 0;
     bool keys_ready = false;   // the greedy step already wrote the own keys
     const bool step_out = (R.flags & kFlagStepOut) != 0;
+    uint8_t* nloc = S.nloc;    // [nown]: buffer bit of each own slot after the greedy step
     for (int t = R.t_begin;; ++t) {
         // R1: own keys (F, rank in the current order), sorted and published
         if (!keys_ready)
-            for (int i = tid; i < nown; i += NT)
-                keys[i] = KO::make(ldst(Fs[cur] + perm[r0 + i], false), (uint32_t)(r0 + i));
-        __syncthreads();
-        if (nown <= 2 * NT) {
-            // rank by counting among the own keys (all distinct)
             for (int i = tid; i < nown; i += NT) {
-                const KT k = keys[i];
+                const uint32_t e = perm[pos_of(i)];
+                keys[i] = KO::make(ldst(Fs[cur] + (e & kSlotMask), false), (uint32_t)pos_of(i));
+                nloc[i] = (uint8_t)(e >> 31);
+            }
+        __syncthreads();
+        if (count_rank) {
+            // rank by counting among the own keys (all distinct): tpk aligned
+            // lanes per key, each counting a strided share, summed by shuffles
+            int tpk = 1;
+            while (tpk < 32 && 2 * tpk * nown <= NT) tpk <<= 1;
+            const int sub = lane & (tpk - 1);
+            for (int base = 0; base < nown; base += NT / tpk) {
+                const int i = base + tid / tpk;
+                const KT k = i < nown ? keys[i] : KO::pad();
                 int rk = 0;
-                for (int j = 0; j < nown; ++j) rk += KO::less(keys[j], k) ? 1 : 0;
-                keys_g[r0 + rk] = k;
+                for (int j = sub; j < nown; j += tpk) rk += KO::less(keys[j], k) ? 1 : 0;
+                for (int m = 1; m < tpk; m <<= 1) rk += __shfl_xor_sync(0xffffffffu, rk, m);
+                if (sub == 0 && i < nown) {
+                    keys_g[kb + rk] = k;
+                    skeys[rk] = k;
+                }
             }
         } else {
             for (int i = tid; i < npad; i += NT)
                 if (i >= nown) keys[i] = KO::pad();
             __syncthreads();
             bitonic_sort<KO>(keys, npad);
-            for (int i = tid; i < nown; i += NT) keys_g[r0 + i] = keys[i];
+            for (int i = tid; i < nown; i += NT) keys_g[kb + i] = keys[i];
         }
         if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
 
-        // the best of the population after iteration t - 1: the smallest head
-        if (local == 0) {
-            if (warp == 0) {
-                KT best = KO::pad();
-                for (int c = lane; c < g; c += 32) {
-                    if (seg[c + 1] > seg[c]) {
-                        const KT h = __ldcg(keys_g + seg[c]);
-                        if (KO::less(h, best)) best = h;
-                    }
-                }
+        // R2: distributed ranking.  An other key y lies above exactly the
+        // p = lower_bound(own sorted keys, y) smallest own keys, so own key i
+        // has sum_{p <= i} hist[p] other keys below it (keys are distinct).
+        for (int i = tid; i < nown; i += NT) hist[i] = 0;
+        __syncthreads();
+        for (int j0 = tid; j0 < ps; j0 += 8 * NT) {
+            KT y[8];
+            bool ok[8];
 #pragma unroll
-                for (int m = 16; m; m >>= 1) {
-                    const KT o = shfl_xor_key(best, m);
-                    if (KO::less(o, best)) best = o;
-                }
-                if (lane == 0) *reinterpret_cast<int*>(S.red) = (int)perm[KO::idx(best)];
+            for (int u = 0; u < 8; ++u) {   // eight loads in flight
+                const int j = j0 + u * NT;
+                ok[u] = j < ps && (j < kb || j >= kb + nown);
+                if (ok[u]) y[u] = __ldcg(keys_g + j);
             }
-            __syncthreads();
-            const int bslot = *reinterpret_cast<int*>(S.red);
-            const FitT fb = ldst(Fs[cur] + bslot, false);
-            if (tid == 0 && R.curve) R.curve[t - 1] = (float)fb;
-            if (t > R.t_end && !step_out) {
-                if (tid == 0 && R.best_f) *R.best_f = (double)fb;
-                if (R.best_x)
-                    for (int d = tid; d < D; d += NT) R.best_x[d] = ldst(Xs[cur] + (size_t)bslot * Dp + d, false);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (ok[u]) {
+                    const int p = lower_bound_key<FitT>(skeys, nown, y[u]);
+                    if (p < nown) atomicAdd(&hist[p], 1);
+                }
+        }
+        __syncthreads();
+        block_scan_inclusive(hist, nown, reinterpret_cast<int*>(S.red));
+        for (int i = tid; i < nown; i += NT) {
+            const int pos = (int)KO::idx(skeys[i]);   // previous rank, an own position
+            R.perm_g[i + hist[i]] = (perm[pos] & kSlotMask) | ((uint32_t)nloc[(pos - local) / g] << 31);
+        }
+        if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
+
+        // R3: the new permutation; its head is the best of iteration t - 1
+        copy_cg(perm, R.perm_g, ps);
+        __syncthreads();
+        if (local == 0) {
+            const uint32_t eb = perm[0];
+            const int bslot = (int)(eb & kSlotMask);
+            if (tid == 0 && R.curve) R.curve[t - 1] = (float)ldst(Fs[cur] + bslot, false);
+            if (t > R.t_end) {
+                if (tid == 0 && R.best_f) *R.best_f = (double)ldst(Fs[cur] + bslot, false);
+                if (R.best_x) {
+                    const float* xb = Xs[eb >> 31] + (size_t)bslot * Dp;
+                    for (int d = tid; d < D; d += NT) R.best_x[d] = ldst(xb + d, false);
+                }
             }
         }
         if (t > R.t_end) break;
 
-        // R2: distributed ranking -- new rank = position in the own segment +
-        // lower bound in every other segment (one warp per key, lanes over segments)
-        copy_cg(keys, keys_g, ps);
-        __syncthreads();
-        for (int i = warp; i < nown; i += nw) {
-            const KT k = keys[r0 + i];
-            int cnt = 0;
-            for (int c = lane; c < g; c += 32)
-                if (c != local) cnt += lower_bound_key<FitT>(keys + seg[c], seg[c + 1] - seg[c], k);
-            cnt = __reduce_add_sync(0xffffffffu, cnt) + i;
-            if (lane == 0) R.perm_g[cnt] = perm[KO::idx(k)];
-        }
-        if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
-
-        // R3: the new permutation, then the own rank range
-        copy_cg(perm, R.perm_g, ps);
-        __syncthreads();
-        for (int c0 = r0; c0 < r1; c0 += CH) {
-            const int rows = min(CH, r1 - c0);
+        // the own positions: generate, evaluate, replace
+        for (int c0 = 0; c0 < nown; c0 += CH) {
+            const int rows = min(CH, nown - c0);
             for (int row = warp; row < rows; row += nw)
-                gen_step_row<FitT, QPL>(R, S, Xs[cur], Fs[cur], perm, false, t, c0 + row, row);
+                gen_step_row<FitT, QPL>(R, S, Xs[0], Xs[1], Fs[cur], perm, false, false, t, pos_of(c0 + row), row);
             __syncthreads();
             eval_chunk<FitT>(R, S, rows);
-            // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i);
-            // the kept fitness also forms the own sort key of the next iteration.
+            // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i).
+            // An accepted row goes to the slot's other buffer (nobody reads it
+            // in this iteration) and flips the slot's buffer bit; a rejected
+            // one stays where it is.  The kept fitness also forms the own sort
+            // key of the next iteration.
             for (int row = warp; row < rows; row += nw) {
-                const int slot = (int)perm[c0 + row];
+                const uint32_t e = perm[pos_of(c0 + row)];
+                const int slot = (int)(e & kSlotMask);
+                const uint32_t loc = e >> 31;
                 const FitT fo = S.rowF[CH + row];
                 const FitT fn = S.rowF[row];
                 const bool acc = fn < fo;
-                const float4* src = reinterpret_cast<const float4*>((acc ? S.Xc : S.Xo) + (size_t)row * Dp);
-                float4* dst = reinterpret_cast<float4*>(Xs[cur ^ 1] + (size_t)slot * Dp);
-                for (int v = lane; v < (Dp >> 2); v += 32) dst[v] = src[v];
+                if (acc) {
+                    const float4* src = reinterpret_cast<const float4*>(S.Xc + (size_t)row * Dp);
+                    float4* dst = reinterpret_cast<float4*>(Xs[loc ^ 1u] + (size_t)slot * Dp);
+                    for (int v = lane; v < (Dp >> 2); v += 32) dst[v] = src[v];
+                }
                 if (lane == 0) {
                     Fs[cur ^ 1][slot] = acc ? fn : fo;
-                    keys[c0 + row - r0] = KO::make(acc ? fn : fo, (uint32_t)(c0 + row));
+                    keys[c0 + row] = KO::make(acc ? fn : fo, (uint32_t)pos_of(c0 + row));
+                    nloc[c0 + row] = (uint8_t)(acc ? (loc ^ 1u) : loc);
                 }
             }
             __syncthreads();
@@ -506,9 +564,11 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
         if (step_out && t == R.t_end) {
             float* xo = R.X_out;
             FitT* fo = static_cast<FitT*>(R.F_out);
-            for (int r = r0 + warp; r < r1; r += nw) {
-                const int slot = (int)perm[r];
-                for (int d = lane; d < D; d += 32) xo[(size_t)r * D + d] = ldst(Xs[cur] + (size_t)slot * Dp + d, false);
+            for (int m = warp; m < nown; m += nw) {
+                const int r = pos_of(m);
+                const int slot = (int)(perm[r] & kSlotMask);
+                const float* src = Xs[nloc[m]] + (size_t)slot * Dp;
+                for (int d = lane; d < D; d += 32) xo[(size_t)r * D + d] = ldst(src + d, false);
                 if (lane == 0) fo[r] = ldst(Fs[cur] + slot, false);
             }
             break;

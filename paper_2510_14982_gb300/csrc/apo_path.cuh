@@ -25,7 +25,7 @@ struct Smem {
     long long *P0, *P1;
     int* otsu;
     void* red;
-    int* seg;
+    uint8_t* nloc;
 };
 
 template <typename FitT>
@@ -46,6 +46,7 @@ __device__ __forceinline__ Smem<FitT> carve(unsigned char* base, const SmemPlan&
     S.ew = reinterpret_cast<float*>(base + L.ew);
     S.Xc = reinterpret_cast<float*>(base + L.Xc);
     S.Xo = reinterpret_cast<float*>(base + L.Xo);
+    S.nloc = reinterpret_cast<uint8_t*>(base + L.nloc);
     S.Yc = reinterpret_cast<float*>(base + L.Yc);
     S.Zc = reinterpret_cast<float*>(base + L.Zc);
     S.rowF = reinterpret_cast<FitT*>(base + L.rowF);
@@ -55,7 +56,6 @@ __device__ __forceinline__ Smem<FitT> carve(unsigned char* base, const SmemPlan&
     S.P1 = reinterpret_cast<long long*>(base + L.P1);
     S.otsu = reinterpret_cast<int*>(base + L.otsu);
     S.red = base + L.red;
-    S.seg = reinterpret_cast<int*>(base + L.seg);
     return S;
 }
 
@@ -327,14 +327,17 @@ __device__ __forceinline__ void gen_init_row(const ApoRun& R, const Smem<FitT>& 
 // Algorithm 1), masks (Eq. 3, Eq. 5), dormancy (Eq. 1), reproduction
 // (Eq. 2), autotrophic (Eq. 6-7) or heterotrophic (Eq. 8-10) foraging, then
 // the bound clamp.  Writes row `row` of Xc (candidate) and of Xo (the old
-// position, kept for the greedy replacement).  The per-protozoon draws are
+// position, kept for the greedy replacement, when keep_old).  Population rows
+// are addressed through perm entries: slot | buffer bit (kLocBit), the bit
+// choosing X1 over X where X1 is given (grid mode keeps each slot's current
+// row in one of two buffers).  The per-protozoon draws are
 // computed once per warp, one Philox call per lane; the gathered rows are
 // requested before the per-dimension draws and the mask selection so that
 // their latency overlaps that arithmetic.
 template <typename FitT, int QPL>
 __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* __restrict__ X,
-                             const FitT* __restrict__ F, const uint32_t* perm, bool res, int t,
-                             int r, int row, int cand = 0)
+                             const float* __restrict__ X1, const FitT* __restrict__ F, const uint32_t* perm,
+                             bool res, bool keep_old, int t, int r, int row, int cand = 0)
 {
     // candidate c of the surrogate-assisted form draws from slots | (c << 8);
     // c = 0 is the plain candidate
@@ -360,28 +363,34 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     const bool forage = mode == kAutotrophic || mode == kHeterotrophic;
 
     // rows from the snapshot: X_i, X_j (autotrophic) and the first pair
-    const int si = (int)perm[r];
-    int sj = si, sa = si, sb = si;
+    auto row_of = [&](uint32_t e) -> const float2* {
+        const float* base = (X1 != nullptr && (e & kLocBit)) ? X1 : X;
+        return reinterpret_cast<const float2*>(base + (size_t)(e & kSlotMask) * Dp);
+    };
+    const uint32_t ei = perm[r];
+    uint32_t ej = ei, ea = ei, eb = ei;
     if (mode == kAutotrophic) {
-        sj = (int)perm[idx_draw(sc2.y, (uint32_t)ps)];
+        ej = perm[idx_draw(sc2.y, (uint32_t)ps)];
         const uint32_t p0 = __shfl_sync(0xffffffffu, jw.x, 2), p1 = __shfl_sync(0xffffffffu, jw.y, 2);
-        sa = (int)perm[idx_draw(p0, (uint32_t)ps)];
-        sb = (int)perm[idx_draw(p1, (uint32_t)ps)];
+        ea = perm[idx_draw(p0, (uint32_t)ps)];
+        eb = perm[idx_draw(p1, (uint32_t)ps)];
     } else if (mode == kHeterotrophic) {
-        sa = (int)perm[r - 1 < 0 ? 0 : r - 1];
-        sb = (int)perm[r + 1 > ps - 1 ? ps - 1 : r + 1];
+        ea = perm[r - 1 < 0 ? 0 : r - 1];
+        eb = perm[r + 1 > ps - 1 ? ps - 1 : r + 1];
     }
+    const int si = (int)(ei & kSlotMask), sa = (int)(ea & kSlotMask), sb = (int)(eb & kSlotMask);
+    const float2 *pi = row_of(ei), *pj = row_of(ej), *pa = row_of(ea), *pb = row_of(eb);
     float xi[2 * QPL], xj[2 * QPL], xa[2 * QPL], xb[2 * QPL];
 #pragma unroll
     for (int j = 0; j < QPL; ++j) {
         const int q = lane + 32 * j;
         float2 vi = make_float2(0.f, 0.f), vj = vi, va = vi, vb = vi;
         if (2 * q < D) {
-            vi = ldst(reinterpret_cast<const float2*>(X + (size_t)si * Dp) + q, res);
-            if (mode == kAutotrophic) vj = ldst(reinterpret_cast<const float2*>(X + (size_t)sj * Dp) + q, res);
+            vi = ldst(pi + q, res);
+            if (mode == kAutotrophic) vj = ldst(pj + q, res);
             if (forage) {
-                va = ldst(reinterpret_cast<const float2*>(X + (size_t)sa * Dp) + q, res);
-                vb = ldst(reinterpret_cast<const float2*>(X + (size_t)sb * Dp) + q, res);
+                va = ldst(pa + q, res);
+                vb = ldst(pb + q, res);
             }
         }
         xi[2 * j] = vi.x; xi[2 * j + 1] = vi.y;
@@ -396,7 +405,8 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     }
     if (lane == 0) S.rowF[R.plan.chunk + row] = ldst(F + si, res);   // old fitness for the greedy step
 
-    // per-dimension draws and the mask (independent of the gathered rows)
+    // per-dimension draws and the mask (independent of the gathered rows,
+    // overlapping their latency)
     uint32_t A[2 * QPL], B[2 * QPL];
     uint32_t valid = 0;
 #pragma unroll
@@ -414,10 +424,10 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     uint32_t mask = 0;
     if (mode == kReproduction) {
         const int k = (int)(((unsigned long long)D * m24p1(sc2.x) + 0xFFFFFFull) >> 24);
-        mask = warp_kselect<QPL>(B, valid, k);
+        mask = warp_kselect_interp<QPL>(B, valid, k, D);
     } else if (forage) {
         const int k = (D * (r + 1) + ps - 1) / ps;
-        mask = warp_kselect<QPL>(B, valid, k);
+        mask = warp_kselect_interp<QPL>(B, valid, k, D);
     }
 
     // Eq. 7 / Eq. 10 weights and the pair sums
@@ -437,19 +447,21 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
                     p0 = pr.x;
                     p1 = pr.y;
                 }
-                sa = (int)perm[idx_draw(p0, (uint32_t)ps)];
-                sb = (int)perm[idx_draw(p1, (uint32_t)ps)];
+                ea = perm[idx_draw(p0, (uint32_t)ps)];
+                eb = perm[idx_draw(p1, (uint32_t)ps)];
             } else {
-                sa = (int)perm[r - k < 0 ? 0 : r - k];
-                sb = (int)perm[r + k > ps - 1 ? ps - 1 : r + k];
+                ea = perm[r - k < 0 ? 0 : r - k];
+                eb = perm[r + k > ps - 1 ? ps - 1 : r + k];
             }
-            const float w2 = expf(-fabsf((float)ldst(F + sa, res) / ((float)ldst(F + sb, res) + kEps)));
+            const float w2 = expf(-fabsf((float)ldst(F + (ea & kSlotMask), res) /
+                                         ((float)ldst(F + (eb & kSlotMask), res) + kEps)));
+            const float2 *qa = row_of(ea), *qb = row_of(eb);
 #pragma unroll
             for (int j = 0; j < QPL; ++j) {
                 const int q = lane + 32 * j;
                 if (2 * q < D) {
-                    const float2 va = ldst(reinterpret_cast<const float2*>(X + (size_t)sa * Dp) + q, res);
-                    const float2 vb = ldst(reinterpret_cast<const float2*>(X + (size_t)sb * Dp) + q, res);
+                    const float2 va = ldst(qa + q, res);
+                    const float2 vb = ldst(qb + q, res);
                     acc[2 * j] = fmaf(w2, va.x - vb.x, acc[2 * j]);
                     acc[2 * j + 1] = fmaf(w2, va.y - vb.y, acc[2 * j + 1]);
                 }
@@ -492,10 +504,10 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
                     }
                 }
                 xc[d] = fminf(fmaxf(x, lb), ub);
-                xo[d] = x0;
+                if (keep_old) xo[d] = x0;
             } else if (d < Dp) {
                 xc[d] = 0.f;
-                xo[d] = 0.f;
+                if (keep_old) xo[d] = 0.f;
             }
         }
     }

@@ -54,7 +54,7 @@ inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool
     L.ub = take(Dp * 4);
     L.ew = take(Dp * 4);
     L.Xc = take(ch * Dp * 4);
-    L.Xo = take(ch * Dp * 4);
+    L.Xo = take(grid ? 0 : ch * Dp * 4);                // grid mode copies no unchanged rows
     L.Yc = take(ch * Dp * 4);                          // transposed: [Dp][chunk]
     L.Zc = take(P->any_rot ? ch * Np * 4 : 0);          // [chunk][Np]
     L.rowF = take(2 * ch * fsz);   // new fitness | old fitness of the chunk rows
@@ -64,7 +64,7 @@ inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool
     L.P1 = take(fit64 ? 256 * 8 : 0);
     L.otsu = take(fit64 ? kMaxWarps * 32 * 4 : 0);
     L.red = take((size_t)L.threads * 16);
-    L.seg = take(grid ? (size_t)(kMaxGridCtas + 1) * 4 : 0);
+    L.nloc = take(grid ? (size_t)L.ps_pad : 0);         // buffer bit of each own slot after the greedy step
     L.total = (uint32_t)plan_align(off, 16);
     return L;
 }
