@@ -580,8 +580,11 @@ def main():
         "true_evals_per_s": evals / (total_ms * 1e-3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": None,
-                     "kernel": "%s (FP32 FMA rotation, 2 D^2 flop per evaluation)" % (
-                         "grid_kernel" if ps > 1024 or (n == 1 and ps >= 128) else "run_kernel"),
+                     "kernel": "%s: rotation on the tensor cores (3-term fp16 split, fp32 accumulation); "
+                               "achieved = 2 D^2 rotation flop per evaluation (FP32-equivalent) / kernel time, "
+                               "against the FP32 lane peak; the kernel is issue-bound in candidate generation "
+                               "and ranking" % ("grid_kernel" if ps > 1024 or (n == 1 and ps >= 128) else "run_kernel"),
+                     "tensor_frac": achieved / (float(pk.get("bf16_tflops", 1894.6))),
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s clock)" % (
                          float(pk.get("sm_max_mhz", 2070.0)), pk["source"]),
                      "kernel_ms": statistics.mean(run_ms)},

@@ -13,6 +13,8 @@
 #include <utility>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "../../include/apo.h"
 #include "apo_internal.h"
 #include "apo_plan.h"
@@ -110,6 +112,23 @@ void apo::set_last_error(const char* msg) { set_err("%s", msg); }
 // ---------------------------------------------------------- problems
 namespace {
 
+// 2^(target - e) for v < 2^e: brings max |value| = v just below 2^target
+// (1 for v == 0).  A power of two, so scaling by it is exact.
+float pow2_scale(double v, int target)
+{
+    if (!(v > 0.0)) return 1.f;
+    int e = 0;
+    std::frexp(v, &e);
+    e = std::min(std::max(target - e, -100), 100);
+    return (float)std::ldexp(1.0, e);
+}
+
+uint16_t half_bits(__half h)
+{
+    const __half_raw r = h;
+    return r.x;
+}
+
 int form_of_component(int kind, int k) { return kind == APO_OBJ_COMPOSITION ? 1 + (k % 4) : kind; }
 
 // ceil(0.3 D) / ceil(0.3 D) / rest split of the hybrid form.
@@ -187,6 +206,8 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
 
     const int Dp = (D + 3) & ~3;
     const int Np = (D + 15) & ~15;
+    const int Kp = (D + 15) & ~15;
+    const int bws = Kp / 2 + 4;   // 4 mod 8 words per column: conflict-free B fragment loads
     // Host image of every device array, laid out in one allocation.
     std::vector<std::pair<size_t, std::vector<unsigned char>>> pieces;
     size_t off = 0;
@@ -202,7 +223,8 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
     std::vector<float> lbf(Dp, 0.f), ubf(Dp, 0.f);
     for (int d = 0; d < D; ++d) { lbf[d] = (float)lb[d]; ubf[d] = (float)ub[d]; }
     const size_t off_lb = add(lbf.data(), Dp * 4), off_ub = add(ubf.data(), Dp * 4);
-    size_t off_o[kMaxComp] = {}, off_mt[kMaxComp] = {}, off_ew[kMaxComp] = {};
+    size_t off_o[kMaxComp] = {}, off_mt[kMaxComp] = {}, off_ew[kMaxComp] = {}, off_bh[kMaxComp] = {},
+           off_bl[kMaxComp] = {};
     bool has_mt[kMaxComp] = {};
     DevComp comps[kMaxComp] = {};
     int any_rot = 0;
@@ -227,6 +249,31 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
             off_mt[k] = add(mt.data(), (size_t)Dp * Np * 4);
             has_mt[k] = true;
             any_rot = 1;
+            // The tensor-core copy: B[k][n] = msc MT[k][n] split into fp16
+            // hi + lo, per column n as k pairs (lower half = even k).  msc
+            // brings max |B| below 2^12 and ysc the largest |x - o| over the
+            // box below 2^10 (64x headroom for points outside the box), so
+            // every part and product stays inside the fp16 / fp32 ranges.
+            double mmax = 0.0, ymax = 0.0;
+            for (float v : mt) mmax = std::max(mmax, (double)std::fabs(v));
+            for (int d = 0; d < D; ++d)
+                ymax = std::max(ymax, std::max(std::fabs((double)ubf[d] - (double)o[d]),
+                                               std::fabs((double)lbf[d] - (double)o[d])));
+            const float msc = pow2_scale(mmax, 12), ysc = pow2_scale(ymax, 10);
+            std::vector<uint32_t> bh((size_t)Np * bws, 0u), bl((size_t)Np * bws, 0u);
+            for (int n = 0; n < D; ++n)
+                for (int kk = 0; kk < D; ++kk) {
+                    const float v = mt[(size_t)kk * Np + n] * msc;
+                    const __half hh = __float2half_rn(v);
+                    const __half ll = __float2half_rn(v - __half2float(hh));
+                    const uint32_t sh = (kk & 1) ? 16u : 0u;
+                    bh[(size_t)n * bws + kk / 2] |= (uint32_t)half_bits(hh) << sh;
+                    bl[(size_t)n * bws + kk / 2] |= (uint32_t)half_bits(ll) << sh;
+                }
+            off_bh[k] = add(bh.data(), bh.size() * 4);
+            off_bl[k] = add(bl.data(), bl.size() * 4);
+            comps[k].ysc = ysc;
+            comps[k].zsc = 1.f / (ysc * msc);   // a power of two: exact
         }
         int s1 = 0, s2 = 0, nell = 0;
         switch (form) {
@@ -318,13 +365,15 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
     }
     DevProblem& dp = P->dev;
     std::memset(&dp, 0, sizeof(dp));
-    dp.D = D; dp.Dp = Dp; dp.Np = Np; dp.kind = kind; dp.ncomp = ncomp;
+    dp.D = D; dp.Dp = Dp; dp.Np = Np; dp.kind = kind; dp.ncomp = ncomp; dp.bws = bws;
     dp.lb = reinterpret_cast<const float*>(base + off_lb);
     dp.ub = reinterpret_cast<const float*>(base + off_ub);
     for (int k = 0; k < ncomp; ++k) {
         dp.comp[k] = comps[k];
         dp.comp[k].o = reinterpret_cast<const float*>(base + off_o[k]);
         dp.comp[k].MT = has_mt[k] ? reinterpret_cast<const float*>(base + off_mt[k]) : nullptr;
+        dp.comp[k].Bh = has_mt[k] ? reinterpret_cast<const uint32_t*>(base + off_bh[k]) : nullptr;
+        dp.comp[k].Bl = has_mt[k] ? reinterpret_cast<const uint32_t*>(base + off_bl[k]) : nullptr;
         dp.comp[k].ew = reinterpret_cast<const float*>(base + off_ew[k]);
     }
     if (kind == APO_OBJ_OTSU) {

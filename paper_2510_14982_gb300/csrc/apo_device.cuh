@@ -47,6 +47,13 @@ constexpr int kFlagStepOut = 2;   // write the rank-ordered state to X_out / F_o
 struct DevComp {
     const float* o;      // [Dp]
     const float* MT;     // [Dp][Np] transposed rotation, zero padded; nullptr = identity
+    // The rotation for the tensor cores: B[k][n] = MT[k][n] * msc split into
+    // fp16 high and low parts (hi + lo = B to 22 bits), stored per column n
+    // as bws words of k pairs (the lower half holds the even k), zero padded.
+    const uint32_t* Bh;
+    const uint32_t* Bl;
+    float ysc;           // power of two bringing |x - o| over the box near 2^14
+    float zsc;           // 1 / (ysc * msc): z = zsc * (ysc (x - o)) . B
     const float* ew;     // [Dp] elliptic weights of the first segment
     int s1, s2;
     float inv_2Dsig2;    // 1 / (2 D sigma^2) (composition)
@@ -55,6 +62,7 @@ struct DevComp {
 
 struct DevProblem {
     int D, Dp, Np, kind, ncomp;  // Dp = D rounded up to 4, Np = D rounded up to 16
+    int bws;             // words per column of Bh / Bl: Kp / 2 + 4 (Kp = D rounded up to 16)
     const float* lb;     // [Dp]
     const float* ub;     // [Dp]
     DevComp comp[kMaxComp];
@@ -254,6 +262,19 @@ __device__ uint32_t warp_kselect(const uint32_t (&key)[2 * QPL], uint32_t valid,
     return sel;
 }
 
+// floor((2^32 - 1) / b) for b = 1 .. 2 (256 + 1): fixed-point reciprocals of
+// the interpolation denominators (slot 0 unused)
+struct RecipTable {
+    uint32_t v[516];
+};
+constexpr RecipTable make_recip_table()
+{
+    RecipTable t{};
+    for (int b = 1; b < 516; ++b) t.v[b] = (uint32_t)(0xFFFFFFFFull / (unsigned long long)b);
+    return t;
+}
+static __constant__ RecipTable kRecip = make_recip_table();
+
 // The same subset as warp_kselect, found by interpolation: a threshold T with
 // exactly k valid keys below it selects the k smallest (every key below T is
 // smaller than every key at or above it, so index tie-breaks cannot arise).
@@ -261,32 +282,35 @@ __device__ uint32_t warp_kselect(const uint32_t (&key)[2 * QPL], uint32_t valid,
 // bracketing counts usually lands between the k-th and (k+1)-th smallest key
 // within a few warp-wide counts (about 3.2 on average for D in 10..200).  A
 // boundary tie, or no hit within ten counts (about 0.3% of selections),
-// falls back to the bitwise descent.  n = number of valid slots.
+// falls back to the bitwise descent.  n = number of valid slots (<= 256).
 template <int QPL>
 __device__ uint32_t warp_kselect_interp(const uint32_t (&key)[2 * QPL], uint32_t valid, int k, int n)
 {
     if (k <= 0) return 0;
     if (k >= n) return valid;
-    // invariant: clo = #(keys < lo) < k < chi = #(keys < hi)
-    unsigned long long lo = 0ull, hi = 1ull << 32;
+    // invariant: clo = #(keys < lo) < k < chi = #(keys <= hm); thresholds are
+    // tried in (lo, hm].  Integer arithmetic only (fixed-point fraction), so
+    // the dependent chain of a step stays on the integer pipes.
+    uint32_t lo = 0u, hm = 0xFFFFFFFFu;
     int clo = 0, chi = n;
 #pragma unroll 1
-    for (int it = 0; it < 10 && hi - lo >= 2ull; ++it) {
+    for (int it = 0; it < 10 && hm > lo; ++it) {
         // the boundary between the (k-clo)-th and (k-clo+1)-th of the chi-clo
-        // keys in [lo, hi) sits near the fraction (k - clo + 1/2) / (chi - clo + 1)
-        const float frac = ((float)(k - clo) + 0.5f) / (float)(chi - clo + 1);
-        unsigned long long T = lo + __float2ull_rz((float)(hi - lo) * frac);
-        if (T <= lo) T = lo + 1ull;
-        if (T >= hi) T = hi - 1ull;
-        const uint32_t t32 = (uint32_t)T;
+        // keys in the bracket sits near the fraction (k - clo + 1/2) / (chi - clo + 1)
+        // = a / b, with a < b, so a * floor((2^32 - 1) / b) < 2^32
+        const uint32_t a = 2u * (uint32_t)(k - clo) + 1u, b = 2u * (uint32_t)(chi - clo + 1);
+        const uint32_t span = hm - lo;
+        uint32_t off = __umulhi(span, a * kRecip.v[b]);
+        off = off < 1u ? 1u : (off > span ? span : off);
+        const uint32_t T = lo + off;
         uint32_t below = 0;
 #pragma unroll
         for (int e = 0; e < 2 * QPL; ++e)
-            if (((valid >> e) & 1u) && key[e] < t32) below |= 1u << e;
+            if (((valid >> e) & 1u) && key[e] < T) below |= 1u << e;
         const int c = __reduce_add_sync(0xffffffffu, __popc(below));
         if (c == k) return below;
         if (c < k) { lo = T; clo = c; }
-        else { hi = T; chi = c; }
+        else { hm = T - 1u; chi = c; }
     }
     return warp_kselect<QPL>(key, valid, k);
 }

@@ -4,6 +4,8 @@
 // rotation GEMM, the objective epilogues and the evaluation of a chunk.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "apo_device.cuh"
 
 namespace apo {
@@ -73,10 +75,16 @@ __device__ __forceinline__ void load_constants(const ApoRun& R, const Smem<FitT>
         S.o[i] = C.o ? C.o[i] : 0.f;
         S.ew[i] = C.ew ? C.ew[i] : 1.f;
     }
-    if (R.plan.mt_smem && C.MT) {
-        const float4* src = reinterpret_cast<const float4*>(C.MT);
-        float4* dst = reinterpret_cast<float4*>(S.MT);
-        for (int i = threadIdx.x; i < Dp * P.Np / 4; i += blockDim.x) dst[i] = src[i];
+    if (R.plan.mt_smem && C.Bh) {
+        // split rotation: Bh then Bl, Np * bws words each (multiples of 4)
+        const int n4 = P.Np * P.bws / 4;
+        const uint4* sh = reinterpret_cast<const uint4*>(C.Bh);
+        const uint4* sl = reinterpret_cast<const uint4*>(C.Bl);
+        uint4* dst = reinterpret_cast<uint4*>(S.MT);
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+            dst[i] = sh[i];
+            dst[n4 + i] = sl[i];
+        }
     }
     if (P.kind == kOtsu) {
         for (int i = threadIdx.x; i < 256; i += blockDim.x) {
@@ -96,19 +104,18 @@ __device__ __forceinline__ float4 lds4(uint32_t addr)
 }
 
 // Z[rows][Np] = Y[rows][Dp] * MT[Dp][Np] with Y stored transposed (YT[k][row],
-// row stride CH) and both operands zero padded beyond D.  FP32 FMA.  A warp
+// row stride CH) and both operands zero padded beyond D.  FP32 FMA (the
+// composition's components, whose rotations stay in global memory).  A warp
 // computes an 8-row x 128-column tile, lane L the columns 4L..4L+3 of the 8
 // rows: per k the 8 row values are two broadcast 16-byte loads shared by the
-// whole warp and the columns one 16-byte load per lane.  MT_SHARED selects a
-// rotation held in shared memory (explicit ld.shared) or read through L1.
-template <bool MT_SHARED, int TR>
+// whole warp and the columns one 16-byte load per lane (through L1).
+template <int TR>
 __device__ __forceinline__ void tile_gemm_t(const float* __restrict__ YT, const float* __restrict__ MT,
                                             float* __restrict__ Z, int rows, int Dp, int Np, int CH)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int rt = (rows + TR - 1) / TR, ct = (Np + 127) >> 7;
     const uint32_t yt_s = (uint32_t)__cvta_generic_to_shared(YT);
-    const uint32_t mt_s = MT_SHARED ? (uint32_t)__cvta_generic_to_shared(MT) : 0u;
     for (int tile = warp; tile < rt * ct; tile += nw) {
         const int tr = tile / ct, tc = tile - tr * ct;
         const int rb = TR * tr, c = 128 * tc + 4 * lane;
@@ -124,10 +131,7 @@ __device__ __forceinline__ void tile_gemm_t(const float* __restrict__ YT, const 
             const float4 a0 = lds4(ya);
             const float4 a1 = TR == 8 ? lds4(ya + 16u) : make_float4(0.f, 0.f, 0.f, 0.f);
             float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (col_ok) {
-                if (MT_SHARED) b = lds4(mt_s + 4u * (uint32_t)(k * Np + c));
-                else b = __ldg(reinterpret_cast<const float4*>(MT + (size_t)k * Np + c));
-            }
+            if (col_ok) b = __ldg(reinterpret_cast<const float4*>(MT + (size_t)k * Np + c));
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
 #pragma unroll
             for (int i = 0; i < TR; ++i) {
@@ -148,13 +152,124 @@ __device__ __forceinline__ void tile_gemm_t(const float* __restrict__ YT, const 
 }
 
 // 8-row tiles when they keep every warp busy, 4-row tiles otherwise.
-template <bool MT_SHARED>
 __device__ __forceinline__ void tile_gemm(const float* __restrict__ YT, const float* __restrict__ MT,
                                           float* __restrict__ Z, int rows, int Dp, int Np, int CH)
 {
     const int nw = blockDim.x >> 5, ct = (Np + 127) >> 7;
-    if (((rows + 7) >> 3) * ct >= nw) tile_gemm_t<MT_SHARED, 8>(YT, MT, Z, rows, Dp, Np, CH);
-    else tile_gemm_t<MT_SHARED, 4>(YT, MT, Z, rows, Dp, Np, CH);
+    if (((rows + 7) >> 3) * ct >= nw) tile_gemm_t<8>(YT, MT, Z, rows, Dp, Np, CH);
+    else tile_gemm_t<4>(YT, MT, Z, rows, Dp, Np, CH);
+}
+
+// ------------------------------------------------ tensor-core rotation
+// (a, b) -> fp16 pairs hi = round(a, b), lo = round((a, b) - hi); hi + lo
+// carries 22 significant bits.  The lower half holds a.
+__device__ __forceinline__ void split_f16x2(float a, float b, uint32_t& hi, uint32_t& lo)
+{
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 f = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - f.x, b - f.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// c += a b for one m16n8k16 tile (fp16 inputs, fp32 accumulation).
+__device__ __forceinline__ void mma_f16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <bool SHARED>
+__device__ __forceinline__ uint32_t ldb(const uint32_t* p)
+{
+    return SHARED ? *p : __ldg(p);
+}
+
+// Z[rows][Np] = (Xc - o)[rows][D] * MT[D][Np] on the tensor cores with a
+// three-term fp16 split: with y = ysc (x - o) = y_hi + y_lo and
+// B = msc MT = B_hi + B_lo (each part an fp16 value, hi + lo exact to 22
+// bits), Z = zsc (y_lo B_hi + y_hi B_lo + y_hi B_hi) accumulated in fp32.
+// The dropped y_lo B_lo is below 2^-22 of a product; the power-of-two
+// scales keep every part inside the fp16 range and are undone exactly.
+// A warp takes a 16-row x 32-column tile (four n8 tiles of mma.m16n8k16);
+// its A fragments come straight from the row-major candidate rows (Dp apart,
+// zero beyond D), its B fragments from the pre-split rotation (shared
+// memory or, when it does not fit, global memory: the same arithmetic).
+// Rows at or beyond `rows` are computed from row rows-1 and discarded.
+template <bool B_SHARED>
+__device__ __forceinline__ void tile_gemm_f16x3(const float* __restrict__ Xc, int Dp, const float* __restrict__ o,
+                                                const uint32_t* __restrict__ Bh, const uint32_t* __restrict__ Bl,
+                                                int bws, float ysc, float zsc, float* __restrict__ Z, int Np,
+                                                int rows, int D)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int mtiles = (rows + 15) >> 4, ngroups = (Np + 31) >> 5, ksteps = (D + 15) >> 4;
+    for (int item = warp; item < mtiles * ngroups; item += nw) {
+        const int mt = item % mtiles, ng = item / mtiles;
+        const int r0 = 16 * mt + g, r1 = r0 + 8;
+        const int nb = 32 * ng;
+        const int ntn = min(4, (Np - nb) >> 3);
+        const float* x0 = Xc + (size_t)min(r0, rows - 1) * Dp;
+        const float* x1 = Xc + (size_t)min(r1, rows - 1) * Dp;
+        const uint32_t* bh = Bh + (size_t)(nb + g) * bws + t;
+        const uint32_t* bl = Bl + (size_t)(nb + g) * bws + t;
+        float acc[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+        for (int ks = 0; ks < ksteps; ++ks) {
+            // A elements (r, k0), (r, k0 + 1) and (r, k0 + 8), (r, k0 + 9);
+            // Dp is a multiple of 4, so a pair is either inside the row or past it
+            const int k0 = 16 * ks + 2 * t, k1 = k0 + 8;
+            float2 a00 = make_float2(0.f, 0.f), a10 = a00, a01 = a00, a11 = a00;
+            if (k0 < Dp) {
+                const float2 oo = *reinterpret_cast<const float2*>(o + k0);
+                const float2 u = *reinterpret_cast<const float2*>(x0 + k0);
+                const float2 v = *reinterpret_cast<const float2*>(x1 + k0);
+                a00 = make_float2((u.x - oo.x) * ysc, (u.y - oo.y) * ysc);
+                a10 = make_float2((v.x - oo.x) * ysc, (v.y - oo.y) * ysc);
+            }
+            if (k1 < Dp) {
+                const float2 oo = *reinterpret_cast<const float2*>(o + k1);
+                const float2 u = *reinterpret_cast<const float2*>(x0 + k1);
+                const float2 v = *reinterpret_cast<const float2*>(x1 + k1);
+                a01 = make_float2((u.x - oo.x) * ysc, (u.y - oo.y) * ysc);
+                a11 = make_float2((v.x - oo.x) * ysc, (v.y - oo.y) * ysc);
+            }
+            uint32_t ah[4], al[4];
+            split_f16x2(a00.x, a00.y, ah[0], al[0]);
+            split_f16x2(a10.x, a10.y, ah[1], al[1]);
+            split_f16x2(a01.x, a01.y, ah[2], al[2]);
+            split_f16x2(a11.x, a11.y, ah[3], al[3]);
+            const int p = 8 * ks;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j < ntn) {
+                    const size_t cj = (size_t)(8 * j) * bws + p;
+                    const uint32_t h0 = ldb<B_SHARED>(bh + cj), h1 = ldb<B_SHARED>(bh + cj + 4);
+                    const uint32_t l0 = ldb<B_SHARED>(bl + cj), l1 = ldb<B_SHARED>(bl + cj + 4);
+                    mma_f16(acc[j], al, h0, h1);
+                    mma_f16(acc[j], ah, l0, l1);
+                    mma_f16(acc[j], ah, h0, h1);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j < ntn) {
+                const int c = nb + 8 * j + 2 * t;
+                if (r0 < rows)
+                    *reinterpret_cast<float2*>(Z + (size_t)r0 * Np + c) = make_float2(acc[j][0] * zsc, acc[j][1] * zsc);
+                if (r1 < rows)
+                    *reinterpret_cast<float2*>(Z + (size_t)r1 * Np + c) = make_float2(acc[j][2] * zsc, acc[j][3] * zsc);
+            }
+        }
+    }
 }
 
 // Segmented objective of one row by one warp (z[d * zs]): [0, s1) high-conditioned
@@ -241,6 +356,23 @@ __device__ __forceinline__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S,
         return;
     }
     const int CH = R.plan.chunk, Np = P.Np;
+    if (P.ncomp == 1 && P.comp[0].Bh) {
+        // one rotated component: tensor-core rotation
+        const DevComp& C = P.comp[0];
+        if (R.plan.mt_smem) {
+            const uint32_t* sb = reinterpret_cast<const uint32_t*>(S.MT);
+            tile_gemm_f16x3<true>(S.Xc, Dp, S.o, sb, sb + (size_t)Np * P.bws, P.bws, C.ysc, C.zsc, S.Zc, Np, rows, D);
+        } else {
+            tile_gemm_f16x3<false>(S.Xc, Dp, S.o, C.Bh, C.Bl, P.bws, C.ysc, C.zsc, S.Zc, Np, rows, D);
+        }
+        __syncthreads();
+        for (int row = warp; row < rows; row += nw) {
+            const float v = seg_value(S.Zc + (size_t)row * Np, 1, P.comp[0], S.ew, D);
+            if (lane == 0) S.rowF[row] = (FitT)v;
+        }
+        __syncthreads();
+        return;
+    }
     for (int c = 0; c < P.ncomp; ++c) {
         const DevComp& C = P.comp[c];
         const float* o = (c == 0) ? S.o : C.o;
@@ -251,8 +383,7 @@ __device__ __forceinline__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S,
         }
         __syncthreads();
         if (C.MT) {
-            if (c == 0 && R.plan.mt_smem) tile_gemm<true>(S.Yc, S.MT, S.Zc, rows, Dp, Np, CH);
-            else tile_gemm<false>(S.Yc, C.MT, S.Zc, rows, Dp, Np, CH);
+            tile_gemm(S.Yc, C.MT, S.Zc, rows, Dp, Np, CH);
             __syncthreads();
         }
         const float* ew = (c == 0) ? S.ew : C.ew;
