@@ -275,6 +275,17 @@ typedef struct apo_surrogate_stats {
 apo_status apo_run_surrogate(const apo_problem* prob, const apo_params* params, const apo_surrogate_params* sp,
                              void* stream, float* best_x, double* best_f, float* curve, apo_surrogate_stats* stats);
 
+/* Test hook of the surrogate-assisted form: the k (1..32) candidates of every
+ * protozoon at iteration iter (1..max_iter) from the population d_X [ps][D],
+ * d_F [ps] (device, float32, current order), as the surrogate path generates
+ * them: the population is ranked by the stable (F, index) sort of Algorithm 1
+ * and candidate c of rank r draws from the plain method's Philox slots
+ * | (c << 8), so c = 0 is the plain candidate (Eq. 1-10, clamped).
+ * d_Xcand [ps][k][D] (device) receives candidate c of rank r at row r k + c.
+ * ps <= 4096; float objectives only.  Synchronous. */
+apo_status apo_surrogate_candidates(const apo_problem* prob, const apo_params* params, int iter, int k,
+                                    void* stream, const float* d_X, const float* d_F, float* d_Xcand);
+
 /* Test hook: the device Philox4x32-10 on n counters d_ctr [n*4] with key
  * (key0, key1) into d_out [n*4].  Stream-ordered. */
 apo_status apo_philox4x32_10(const uint32_t* d_ctr, uint32_t key0, uint32_t key1, int n,

@@ -79,6 +79,9 @@ def lib():
         L.orc_apo_step.argtypes = [P(Problem), P(Params), C.c_int, P(C.c_double),
                                    P(C.c_double), P(StepInfo)]
         L.orc_apo_step.restype = C.c_int
+        L.orc_candidates.argtypes = [P(Problem), P(Params), C.c_int, C.c_int, P(C.c_double), P(C.c_double),
+                                     P(C.c_double), P(C.c_int32)]
+        L.orc_candidates.restype = C.c_int
         L.orc_apo_run.argtypes = [P(Problem), P(Params), P(C.c_double), P(C.c_double),
                                   P(C.c_double)]
         L.orc_apo_run_many.argtypes = [P(P(Problem)), P(Params), C.c_int, C.c_int, C.c_int,
@@ -185,6 +188,22 @@ def apo_step(prob: OracleProblem, prm: Params, t, X, F, with_info=False):
         arrs["m"] = int(arrs["m"][0])
         return X, F, arrs
     return X, F
+
+
+def candidates(prob: OracleProblem, prm: Params, t, k, X, F):
+    """Surrogate-assisted form: the k candidates of every protozoon at iteration
+    t (candidate c draws from the plain slots | (c << 8)).  Returns
+    (Xc[ps, k, D] in this iteration's rank order, order[ps])."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    ps, D = prm.ps, prob.D
+    Xc = np.empty((ps, int(k), D), np.float64)
+    order = np.empty(ps, np.int32)
+    rc = lib().orc_candidates(C.byref(prob.c), C.byref(prm), int(t), int(k), _ptr(X, C.c_double),
+                              _ptr(F, C.c_double), _ptr(Xc, C.c_double), _ptr(order, C.c_int32))
+    if rc != 0:
+        raise ValueError("orc_candidates rejected its arguments")
+    return Xc, order
 
 
 def apo_run(prob: OracleProblem, prm: Params, want_curve=True):

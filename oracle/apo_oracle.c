@@ -440,6 +440,119 @@ static double orc_p_dr(int i, int ps, int form)
     return form == 0 ? 0.5 * (1.0 - c) : 0.5 * (1.0 + c);
 }
 
+/* The candidate of rank r (0-based; i = r + 1) at iteration t from the
+ * sorted snapshot (Xs, Fs): mode selection (Eq. 12-13), dormancy (Eq. 1),
+ * reproduction (Eq. 2-3) or foraging (Eq. 4-10), then the bound clamp (R11).
+ * Every per-protozoon draw uses its slot | slot_off: slot_off = c << 8 gives
+ * candidate c of the surrogate-assisted form, 0 the plain method.  in_dr is
+ * the iteration's Dr_index set (Eq. 11).  Writes x (clamped) and, if given,
+ * xraw (before the clamp), *kmask_out and the mask M[D]; returns the mode
+ * (0 dormancy, 1 reproduction, 2 autotrophic, 3 heterotrophic).  Rand[D] and
+ * mkey[D] are scratch. */
+static int orc_candidate(const orc_problem* P, const orc_params* prm, int t, int r, uint32_t slot_off,
+                         const double* Xs, const double* Fs, const uint8_t* in_dr, double* x,
+                         double* xraw, int* kmask_out, uint8_t* M, double* Rand, uint32_t* mkey)
+{
+    const int ps = prm->ps, D = P->D, np = prm->np, T = prm->max_iter;
+    const uint32_t seed = prm->seed, run = prm->run;
+    const double eps = 2.220446049250313e-16; /* 2^-52, reading R4 */
+    /* Eq. 12, Eq. 4 and Eq. 9 schedules. */
+    const double p_ah = orc_p_ah(t, T);
+    const double fscale = 1.0 + cos(((double)t / (double)T) * M_PI);
+    const double nearscale = 1.0 - (double)t / (double)T;
+    const int i = r + 1;
+    const double* Xi = Xs + (size_t)r * D;
+    uint32_t sc[4], sc2[4];
+    orc_draw(seed, run, (uint32_t)t, (uint32_t)r, ORC_ALL, ORC_SLOT_SCAL | slot_off, sc);
+    orc_draw(seed, run, (uint32_t)t, (uint32_t)r, ORC_ALL, ORC_SLOT_SCAL2 | slot_off, sc2);
+    for (int d = 0; d < D; ++d) {
+        uint32_t A, B;
+        orc_dim_words(seed, run, (uint32_t)t, (uint32_t)r, d, ORC_SLOT_DIM | slot_off, &A, &B);
+        Rand[d] = orc_U(A);
+        mkey[d] = B;
+    }
+    const double u_mode = orc_U(sc[0]);
+    int mode, kmask = 0;
+    if (in_dr[r]) {
+        if (orc_p_dr(i, ps, prm->pdr_form) > u_mode) {
+            /* Eq. 1: dormancy -- a fresh protozoon replaces X_i. */
+            mode = 0;
+            for (int d = 0; d < D; ++d)
+                x[d] = P->lb[d] + Rand[d] * (P->ub[d] - P->lb[d]);
+        } else {
+            /* Eq. 2-3: reproduction. */
+            mode = 1;
+            kmask = (int)ceil((double)D * orc_U(sc2[0]));
+            orc_randperm_set(mkey, D, kmask, M);
+            const double s = orc_SIGN(sc[2]);
+            const double rho = orc_U(sc[3]);
+            for (int d = 0; d < D; ++d) {
+                if (M[d])
+                    x[d] = Xi[d] + s * rho * (P->lb[d] + Rand[d] * (P->ub[d] - P->lb[d]));
+                else
+                    x[d] = Xi[d];
+            }
+        }
+    } else {
+        /* Eq. 4-5: foraging factor f and mask M_f. */
+        kmask = (D * i + ps - 1) / ps; /* ceil(D * i / ps) */
+        orc_randperm_set(mkey, D, kmask, M);
+        const double f = orc_U(sc[1]) * fscale;
+        if (p_ah > u_mode) {
+            /* Eq. 6-7: autotrophic foraging. */
+            mode = 2;
+            const int j = (int)orc_IDX(sc2[1], (uint32_t)ps);
+            const double* Xj = Xs + (size_t)j * D;
+            int* km = (int*)malloc(sizeof(int) * (size_t)np);
+            int* kp = (int*)malloc(sizeof(int) * (size_t)np);
+            double* wa = (double*)malloc(sizeof(double) * (size_t)np);
+            for (int k = 1; k <= np; ++k) {
+                uint32_t pr[4];
+                orc_draw(seed, run, (uint32_t)t, (uint32_t)r, (uint32_t)(k - 1),
+                         ORC_SLOT_PAIR | slot_off, pr);
+                km[k - 1] = (int)orc_IDX(pr[0], (uint32_t)ps);
+                kp[k - 1] = (int)orc_IDX(pr[1], (uint32_t)ps);
+                /* Eq. 7 */
+                wa[k - 1] = exp(-fabs(Fs[km[k - 1]] / (Fs[kp[k - 1]] + eps)));
+            }
+            for (int d = 0; d < D; ++d) {
+                if (!M[d]) { x[d] = Xi[d]; continue; }
+                double acc = 0.0;
+                for (int k = 0; k < np; ++k)
+                    acc += wa[k] * (Xs[(size_t)km[k] * D + d] - Xs[(size_t)kp[k] * D + d]);
+                x[d] = Xi[d] + f * (Xj[d] - Xi[d] + acc / (double)np);
+            }
+            free(km); free(kp); free(wa);
+        } else {
+            /* Eq. 8-10: heterotrophic foraging. */
+            mode = 3;
+            const double s = orc_SIGN(sc[2]);
+            for (int d = 0; d < D; ++d) {
+                if (!M[d]) { x[d] = Xi[d]; continue; }
+                /* Eq. 9 */
+                double xnear = (1.0 + s * Rand[d] * nearscale) * Xi[d];
+                double acc = 0.0;
+                for (int k = 1; k <= np; ++k) {
+                    int a = r - k < 0 ? 0 : r - k;          /* R3 */
+                    int b = r + k > ps - 1 ? ps - 1 : r + k;
+                    /* Eq. 10 */
+                    double wh = exp(-fabs(Fs[a] / (Fs[b] + eps)));
+                    acc += wh * (Xs[(size_t)a * D + d] - Xs[(size_t)b * D + d]);
+                }
+                x[d] = Xi[d] + f * (xnear - Xi[d] + acc / (double)np);
+            }
+        }
+    }
+    if (xraw) memcpy(xraw, x, sizeof(double) * (size_t)D);
+    /* Bound handling (R11). */
+    for (int d = 0; d < D; ++d) {
+        if (x[d] < P->lb[d]) x[d] = P->lb[d];
+        if (x[d] > P->ub[d]) x[d] = P->ub[d];
+    }
+    if (kmask_out) *kmask_out = kmask;
+    return mode;
+}
+
 /* One iteration of Algorithm 1 at iteration t (1..max_iter).  X[ps*D], F[ps]
  * are read in their current order and returned in the rank order of this
  * iteration's sort, with the greedy replacement applied. */
@@ -448,7 +561,6 @@ int orc_apo_step(const orc_problem* P, const orc_params* prm, int t, double* X,
 {
     const int ps = prm->ps, D = P->D, np = prm->np, T = prm->max_iter;
     const uint32_t seed = prm->seed, run = prm->run;
-    const double eps = 2.220446049250313e-16; /* 2^-52, reading R4 */
     if (ps < 1 || D < 1 || np < 1 || T < 1) return -1;
 
     /* Algorithm 1: sort X_i, i = 1..ps, by fitness (ascending; R9). */
@@ -478,11 +590,6 @@ int orc_apo_step(const orc_problem* P, const orc_params* prm, int t, double* X,
     orc_randperm_set(drkey, ps, m, in_dr);
     if (info && info->m) info->m[0] = m;
 
-    /* Eq. 12, Eq. 4 and Eq. 9 schedules. */
-    const double p_ah = orc_p_ah(t, T);
-    const double fscale = 1.0 + cos(((double)t / (double)T) * M_PI);
-    const double nearscale = 1.0 - (double)t / (double)T;
-
     double* Xn = (double*)malloc(sizeof(double) * (size_t)ps * D);
     double* Fn = (double*)malloc(sizeof(double) * (size_t)ps);
     double* Rand = (double*)malloc(sizeof(double) * (size_t)D);
@@ -491,97 +598,11 @@ int orc_apo_step(const orc_problem* P, const orc_params* prm, int t, double* X,
 
     /* Parallel for each i = 1:ps (every candidate reads the sorted snapshot). */
     for (int r = 0; r < ps; ++r) {
-        const int i = r + 1;
-        const double* Xi = Xs + (size_t)r * D;
         double* x = Xn + (size_t)r * D;
-        uint32_t sc[4], sc2[4];
-        orc_draw(seed, run, (uint32_t)t, (uint32_t)r, ORC_ALL, ORC_SLOT_SCAL, sc);
-        orc_draw(seed, run, (uint32_t)t, (uint32_t)r, ORC_ALL, ORC_SLOT_SCAL2, sc2);
-        for (int d = 0; d < D; ++d) {
-            uint32_t A, B;
-            orc_dim_words(seed, run, (uint32_t)t, (uint32_t)r, d, ORC_SLOT_DIM, &A, &B);
-            Rand[d] = orc_U(A);
-            mkey[d] = B;
-        }
-        const double u_mode = orc_U(sc[0]);
-        int mode, kmask = 0;
-        if (in_dr[r]) {
-            if (orc_p_dr(i, ps, prm->pdr_form) > u_mode) {
-                /* Eq. 1: dormancy -- a fresh protozoon replaces X_i. */
-                mode = 0;
-                for (int d = 0; d < D; ++d)
-                    x[d] = P->lb[d] + Rand[d] * (P->ub[d] - P->lb[d]);
-            } else {
-                /* Eq. 2-3: reproduction. */
-                mode = 1;
-                kmask = (int)ceil((double)D * orc_U(sc2[0]));
-                orc_randperm_set(mkey, D, kmask, M);
-                const double s = orc_SIGN(sc[2]);
-                const double rho = orc_U(sc[3]);
-                for (int d = 0; d < D; ++d) {
-                    if (M[d])
-                        x[d] = Xi[d] + s * rho * (P->lb[d] + Rand[d] * (P->ub[d] - P->lb[d]));
-                    else
-                        x[d] = Xi[d];
-                }
-            }
-        } else {
-            /* Eq. 4-5: foraging factor f and mask M_f. */
-            kmask = (D * i + ps - 1) / ps; /* ceil(D * i / ps) */
-            orc_randperm_set(mkey, D, kmask, M);
-            const double f = orc_U(sc[1]) * fscale;
-            if (p_ah > u_mode) {
-                /* Eq. 6-7: autotrophic foraging. */
-                mode = 2;
-                const int j = (int)orc_IDX(sc2[1], (uint32_t)ps);
-                const double* Xj = Xs + (size_t)j * D;
-                int* km = (int*)malloc(sizeof(int) * (size_t)np);
-                int* kp = (int*)malloc(sizeof(int) * (size_t)np);
-                double* wa = (double*)malloc(sizeof(double) * (size_t)np);
-                for (int k = 1; k <= np; ++k) {
-                    uint32_t pr[4];
-                    orc_draw(seed, run, (uint32_t)t, (uint32_t)r, (uint32_t)(k - 1),
-                             ORC_SLOT_PAIR, pr);
-                    km[k - 1] = (int)orc_IDX(pr[0], (uint32_t)ps);
-                    kp[k - 1] = (int)orc_IDX(pr[1], (uint32_t)ps);
-                    /* Eq. 7 */
-                    wa[k - 1] = exp(-fabs(Fs[km[k - 1]] / (Fs[kp[k - 1]] + eps)));
-                }
-                for (int d = 0; d < D; ++d) {
-                    if (!M[d]) { x[d] = Xi[d]; continue; }
-                    double acc = 0.0;
-                    for (int k = 0; k < np; ++k)
-                        acc += wa[k] * (Xs[(size_t)km[k] * D + d] - Xs[(size_t)kp[k] * D + d]);
-                    x[d] = Xi[d] + f * (Xj[d] - Xi[d] + acc / (double)np);
-                }
-                free(km); free(kp); free(wa);
-            } else {
-                /* Eq. 8-10: heterotrophic foraging. */
-                mode = 3;
-                const double s = orc_SIGN(sc[2]);
-                for (int d = 0; d < D; ++d) {
-                    if (!M[d]) { x[d] = Xi[d]; continue; }
-                    /* Eq. 9 */
-                    double xnear = (1.0 + s * Rand[d] * nearscale) * Xi[d];
-                    double acc = 0.0;
-                    for (int k = 1; k <= np; ++k) {
-                        int a = r - k < 0 ? 0 : r - k;          /* R3 */
-                        int b = r + k > ps - 1 ? ps - 1 : r + k;
-                        /* Eq. 10 */
-                        double wh = exp(-fabs(Fs[a] / (Fs[b] + eps)));
-                        acc += wh * (Xs[(size_t)a * D + d] - Xs[(size_t)b * D + d]);
-                    }
-                    x[d] = Xi[d] + f * (xnear - Xi[d] + acc / (double)np);
-                }
-            }
-        }
-        if (info && info->xnew_raw)
-            memcpy(info->xnew_raw + (size_t)r * D, x, sizeof(double) * (size_t)D);
-        /* Bound handling (R11). */
-        for (int d = 0; d < D; ++d) {
-            if (x[d] < P->lb[d]) x[d] = P->lb[d];
-            if (x[d] > P->ub[d]) x[d] = P->ub[d];
-        }
+        int kmask = 0;
+        const int mode = orc_candidate(P, prm, t, r, 0u, Xs, Fs, in_dr, x,
+                                       (info && info->xnew_raw) ? info->xnew_raw + (size_t)r * D : NULL,
+                                       &kmask, M, Rand, mkey);
         Fn[r] = orc_objective(P, x);
         if (info) {
             if (info->in_dr) info->in_dr[r] = in_dr[r];
@@ -610,6 +631,52 @@ int orc_apo_step(const orc_problem* P, const orc_params* prm, int t, double* X,
 
     free(Xs); free(Fs); free(drkey); free(in_dr); free(Xn); free(Fn);
     free(Rand); free(mkey); free(M);
+    return 0;
+}
+
+/* Surrogate-assisted form: the k candidates of every protozoon at iteration
+ * t, from X[ps*D], F[ps] in their current order.  The population is sorted
+ * and Dr_index drawn as in orc_apo_step; candidate c of rank r draws from the
+ * plain slots | (c << 8) (c = 0 is the plain candidate) and is written,
+ * clamped, to Xc[(r*k + c)*D ...].  order[r] (optional) = current index of
+ * rank r.  Returns 0, or -1 for invalid sizes. */
+int orc_candidates(const orc_problem* P, const orc_params* prm, int t, int k, const double* X,
+                   const double* F, double* Xc, int32_t* order)
+{
+    const int ps = prm->ps, D = P->D;
+    const uint32_t seed = prm->seed, run = prm->run;
+    if (ps < 1 || D < 1 || prm->np < 1 || prm->max_iter < 1 || k < 1 || k > 256) return -1;
+    orc_sort_item* it = (orc_sort_item*)malloc(sizeof(orc_sort_item) * (size_t)ps);
+    for (int i = 0; i < ps; ++i) { it[i].f = F[i]; it[i].idx = i; it[i].key = 0; }
+    qsort(it, (size_t)ps, sizeof(orc_sort_item), orc_cmp_fitness);
+    double* Xs = (double*)malloc(sizeof(double) * (size_t)ps * D);
+    double* Fs = (double*)malloc(sizeof(double) * (size_t)ps);
+    for (int r = 0; r < ps; ++r) {
+        memcpy(Xs + (size_t)r * D, X + (size_t)it[r].idx * D, sizeof(double) * (size_t)D);
+        Fs[r] = F[it[r].idx];
+        if (order) order[r] = it[r].idx;
+    }
+    free(it);
+    /* Eq. 11: the iteration's Dr_index, shared by all candidates. */
+    uint32_t w[4];
+    orc_draw(seed, run, (uint32_t)t, ORC_ALL, ORC_ALL, ORC_SLOT_PF, w);
+    const double pf = prm->pf_max * orc_U(w[0]);
+    const int m = (int)ceil((double)ps * pf);
+    uint32_t* drkey = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)ps);
+    for (int r = 0; r < ps; ++r) {
+        orc_draw(seed, run, (uint32_t)t, (uint32_t)(r >> 2), ORC_ALL, ORC_SLOT_DR, w);
+        drkey[r] = w[r & 3];
+    }
+    uint8_t* in_dr = (uint8_t*)malloc((size_t)ps);
+    orc_randperm_set(drkey, ps, m, in_dr);
+    double* Rand = (double*)malloc(sizeof(double) * (size_t)D);
+    uint32_t* mkey = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)D);
+    uint8_t* M = (uint8_t*)malloc((size_t)D);
+    for (int r = 0; r < ps; ++r)
+        for (int c = 0; c < k; ++c)
+            orc_candidate(P, prm, t, r, (uint32_t)c << 8, Xs, Fs, in_dr, Xc + ((size_t)r * k + c) * D, NULL, NULL,
+                          M, Rand, mkey);
+    free(Xs); free(Fs); free(drkey); free(in_dr); free(Rand); free(mkey); free(M);
     return 0;
 }
 

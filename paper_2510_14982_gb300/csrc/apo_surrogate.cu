@@ -626,6 +626,85 @@ cudaError_t launch_surr_q(int qpl, int which, dim3 grid, size_t smem, cudaStream
 
 #include "apo_plan.h"
 
+// Test hook: the k candidates of every protozoon at iteration `iter` from a
+// given population, generated by the surrogate path's own sort and
+// candidate kernels (candidate c draws from the plain slots | (c << 8)).
+extern "C" apo_status apo_surrogate_candidates(const apo_problem* P, const apo_params* p, int iter, int k,
+                                               void* stream, const float* d_X, const float* d_F, float* d_Xcand)
+{
+    if (!P || !p || !d_X || !d_F || !d_Xcand) { apo::set_last_error("apo_surrogate_candidates: NULL argument"); return APO_ERR_INVALID_ARG; }
+    if (P->kind == APO_OBJ_OTSU) { apo::set_last_error("apo_surrogate_candidates: float objectives only"); return APO_ERR_UNSUPPORTED; }
+    if (p->ps < 2 || p->np < 1 || 2 * p->np >= p->ps || !(p->pf_max >= 0.0 && p->pf_max <= 1.0) || p->max_iter < 1 ||
+        (p->pdr_form != 0 && p->pdr_form != 1) || iter < 1 || iter > p->max_iter || k < 1 || k > 32) {
+        apo::set_last_error("apo_surrogate_candidates: arguments out of range");
+        return APO_ERR_INVALID_ARG;
+    }
+    if (p->ps > 4096) { apo::set_last_error("apo_surrogate_candidates: ps above 4096"); return APO_ERR_UNSUPPORTED; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int ps = p->ps, T = p->max_iter, D = P->D, Dp = P->Dp;
+    const int ps_pad = plan_pow2(ps);
+    const int qpl = D <= 64 ? 1 : (D <= 128 ? 2 : 4);
+    const SmemPlan plan = choose_plan(P, ps, false, false, 232448 - 2048);
+    const int W = (ps + 31) / 32;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { off = (off + 255) / 256 * 256; const size_t at = off; off += bytes; return at; };
+    const size_t o_run = take(sizeof(ApoRun)), o_offs = take(8), o_dr = take((size_t)(T + 1) * W * 4);
+    const size_t o_x = take((size_t)ps * Dp * 4), o_f = take((size_t)ps * 4);
+    const size_t o_p0 = take((size_t)ps * 4), o_p1 = take((size_t)ps * 4), o_xc = take((size_t)ps * k * Dp * 4);
+    void* ws = nullptr;
+    if (cudaMalloc(&ws, off) != cudaSuccess) { apo::set_last_error("apo_surrogate_candidates: workspace allocation failed"); return APO_ERR_OOM; }
+    unsigned char* b = static_cast<unsigned char*>(ws);
+    ApoRun R;
+    std::memset(&R, 0, sizeof(R));
+    R.prob = P->dev;
+    R.plan = plan;
+    R.ps = ps; R.np = p->np; R.T = T; R.pdr_form = p->pdr_form; R.pf_max = p->pf_max;
+    R.seed = p->seed; R.run = p->run; R.t_begin = iter; R.t_end = iter; R.flags = 0; R.g = 1;
+    apo_status rc = sched_tables(ps, p->pdr_form, T, &R.thr_dr, &R.thr_ah, &R.fsc, &R.nsc);
+    R.drmask = reinterpret_cast<const uint32_t*>(b + o_dr);
+    const int offs[2] = {0, 1};
+    std::vector<uint32_t> ident(ps);
+    std::iota(ident.begin(), ident.end(), 0u);
+    const ApoRun* d_run = reinterpret_cast<const ApoRun*>(b + o_run);
+    float* Xp = reinterpret_cast<float*>(b + o_x);
+    float* Fp = reinterpret_cast<float*>(b + o_f);
+    uint32_t* p0 = reinterpret_cast<uint32_t*>(b + o_p0);
+    uint32_t* p1 = reinterpret_cast<uint32_t*>(b + o_p1);
+    float* Xc = reinterpret_cast<float*>(b + o_xc);
+    cudaError_t e = rc == APO_OK ? cudaSuccess : cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_run, &R, sizeof(R), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_offs, offs, 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p0, ident.data(), (size_t)ps * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Xp, 0, (size_t)ps * Dp * 4, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(Xp, (size_t)Dp * 4, d_X, (size_t)D * 4, (size_t)D * 4, ps, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Fp, d_F, (size_t)ps * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = launch_dr(d_run, reinterpret_cast<const int*>(b + o_offs), 1, 1, ps_pad, st);
+    if (e == cudaSuccess) {
+        const size_t sort_smem = (size_t)ps_pad * 8;
+        if (sort_smem > 48 * 1024)
+            cudaFuncSetAttribute(surr_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
+        surr_sort_kernel<<<1, 1024, sort_smem, st>>>(ps, ps_pad, Fp, p0, p1, nullptr, iter);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = launch_surr_q(qpl, 1, dim3(std::max(1, std::min(1024, (ps * k + plan.chunk - 1) / plan.chunk))), plan.total,
+                          st, d_run, k, k, iter, p1, Xp, Fp, Xc, nullptr, 0, nullptr, nullptr, nullptr, nullptr,
+                          nullptr, 0, 0, nullptr, nullptr);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(d_Xcand, (size_t)D * 4, Xc, (size_t)Dp * 4, (size_t)D * 4, (size_t)ps * k,
+                              cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(ws);
+    if (e != cudaSuccess) {
+        char m[200];
+        snprintf(m, sizeof(m), "apo_surrogate_candidates: %s", cudaGetErrorString(e));
+        apo::set_last_error(m);
+        return APO_ERR_CUDA;
+    }
+    return APO_OK;
+}
+
 extern "C" apo_status apo_run_surrogate(const apo_problem* P, const apo_params* p, const apo_surrogate_params* sp,
                                         void* stream, float* best_x, double* best_f, float* curve,
                                         apo_surrogate_stats* stats)

@@ -44,3 +44,32 @@ def test_screening_bookkeeping(apo):
     assert st["screening_iters"] + 10 + st["fallback_iters"] == T
     assert st["screened"] == ps * (T - st["screening_iters"]) + ps * k * st["screening_iters"]
     assert np.all(np.diff(c) <= 0) and c[-1] == np.float32(f)
+
+
+@pytest.mark.parametrize("mk,ps,t,T,k", [
+    (lambda: inputs.scale_forms(0, 20)[2], 48, 9, 60, 6),          # Rastrigin D 20, several ranks per chunk
+    (lambda: inputs.scale_forms(1, 37)[3], 300, 150, 300, 3),      # hybrid, ragged D 37, ragged ps
+    (lambda: inputs.composition(D=200, seed=0), 256, 40, 300, 8),  # the surrogate workload's problem
+])
+def test_surrogate_candidates_match_oracle(apo, orc, mk, ps, t, T, k):
+    """The k candidates of every protozoon as the surrogate path generates them
+    (slots | (c << 8)) against the oracle's, element by element: the modes,
+    masks and indices are the same integer decisions on both sides, the
+    positions agree within the one-iteration tolerance."""
+    import torch
+    from parity_helpers import close
+    spec = mk()
+    gprob = apo.problem_from_spec(spec)
+    oprob = orc.OracleProblem.from_spec(spec)
+    oprm = orc.params(ps, 1, 0.1, T, 5)
+    gprm = apo.apo_params_make(ps, 1, 0.1, T, 5)
+    X0, _ = orc.init_population(oprob, oprm)
+    X32 = X0.astype(np.float32)
+    F32 = orc.objective(oprob, X32.astype(np.float64)).astype(np.float32)
+    d_X = torch.tensor(X32, device="cuda")
+    d_F = torch.tensor(F32, device="cuda")
+    d_Xc = torch.empty((ps, k, spec.D), device="cuda")
+    apo.apo_surrogate_candidates(gprob, gprm, t, k, d_X, d_F, d_Xc)
+    Xc_o, _ = orc.candidates(oprob, oprm, t, k, X32.astype(np.float64), F32.astype(np.float64))
+    ok = close(d_Xc.cpu().numpy(), Xc_o)
+    assert ok.all(), np.argwhere(~ok)[:10]
