@@ -207,7 +207,7 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
     const int Dp = (D + 3) & ~3;
     const int Np = (D + 15) & ~15;
     const int Kp = (D + 15) & ~15;
-    const int bws = Kp / 2 + 4;   // 4 mod 8 words per column: conflict-free B fragment loads
+    const int bws = split_words(D);
     // Host image of every device array, laid out in one allocation.
     std::vector<std::pair<size_t, std::vector<unsigned char>>> pieces;
     size_t off = 0;
@@ -250,7 +250,8 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
             has_mt[k] = true;
             any_rot = 1;
             // The tensor-core copy: B[k][n] = msc MT[k][n] split into fp16
-            // hi + lo, per column n as k pairs (lower half = even k).  msc
+            // hi + lo, per column n as k pairs (lower half = even k) in the
+            // fragment order of pair_word.  msc
             // brings max |B| below 2^12 and ysc the largest |x - o| over the
             // box below 2^10 (64x headroom for points outside the box), so
             // every part and product stays inside the fp16 / fp32 ranges.
@@ -267,8 +268,8 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
                     const __half hh = __float2half_rn(v);
                     const __half ll = __float2half_rn(v - __half2float(hh));
                     const uint32_t sh = (kk & 1) ? 16u : 0u;
-                    bh[(size_t)n * bws + kk / 2] |= (uint32_t)half_bits(hh) << sh;
-                    bl[(size_t)n * bws + kk / 2] |= (uint32_t)half_bits(ll) << sh;
+                    bh[(size_t)n * bws + pair_word(kk / 2)] |= (uint32_t)half_bits(hh) << sh;
+                    bl[(size_t)n * bws + pair_word(kk / 2)] |= (uint32_t)half_bits(ll) << sh;
                 }
             off_bh[k] = add(bh.data(), bh.size() * 4);
             off_bl[k] = add(bl.data(), bl.size() * 4);

@@ -49,7 +49,8 @@ struct DevComp {
     const float* MT;     // [Dp][Np] transposed rotation, zero padded; nullptr = identity
     // The rotation for the tensor cores: B[k][n] = MT[k][n] * msc split into
     // fp16 high and low parts (hi + lo = B to 22 bits), stored per column n
-    // as bws words of k pairs (the lower half holds the even k), zero padded.
+    // as bws words of k pairs (the lower half holds the even k) in pair_word
+    // order, zero padded.
     const uint32_t* Bh;
     const uint32_t* Bl;
     float ysc;           // power of two bringing |x - o| over the box near 2^14
@@ -62,7 +63,7 @@ struct DevComp {
 
 struct DevProblem {
     int D, Dp, Np, kind, ncomp;  // Dp = D rounded up to 4, Np = D rounded up to 16
-    int bws;             // words per column of Bh / Bl: Kp / 2 + 4 (Kp = D rounded up to 16)
+    int bws;             // words per column of Bh / Bl: split_words(D)
     const float* lb;     // [Dp]
     const float* ub;     // [Dp]
     DevComp comp[kMaxComp];
@@ -70,6 +71,23 @@ struct DevProblem {
     const long long* P1; // Otsu: prefix first moments [256]
     const double* otsu_tab;  // Otsu: between-class term of every bin range [a, b]
 };
+
+// Word of k pair p (k = 2p, 2p + 1) in a row of fp16-pair words laid out for
+// the m16n8k16 fragments: the pairs p and p + 4 of a 16-wide k step (the two
+// registers a lane loads) are adjacent, so a fragment is one 64-bit load.
+__host__ __device__ __forceinline__ int pair_word(int p)
+{
+    return 8 * (p >> 3) + 2 * (p & 3) + ((p >> 2) & 1);
+}
+
+// Words per column of such pairs: Kp / 2 (Kp = D rounded up to 16) raised to
+// 8 mod 16, so that the 64-bit fragment loads of 8 columns x 4 lanes fall on
+// distinct banks.
+__host__ __device__ __forceinline__ int split_words(int D)
+{
+    const int h = ((D + 15) & ~15) / 2;
+    return (h % 16 == 8) ? h : h + 8;
+}
 
 // Packed index of the bin range [a, b] (0 <= a <= b <= 255) in the Otsu term table.
 __host__ __device__ __forceinline__ int otsu_tab_index(int a, int b)

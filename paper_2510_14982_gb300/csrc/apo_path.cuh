@@ -183,9 +183,17 @@ __device__ __forceinline__ void mma_f16(float (&c)[4], const uint32_t (&a)[4], u
 }
 
 template <bool SHARED>
-__device__ __forceinline__ uint32_t ldb(const uint32_t* p)
+__device__ __forceinline__ uint2 ldb2(const uint32_t* p)
 {
-    return SHARED ? *p : __ldg(p);
+    return SHARED ? *reinterpret_cast<const uint2*>(p) : __ldg(reinterpret_cast<const uint2*>(p));
+}
+
+// y = ysc (x - o) for the k pair (x0, x1) of one candidate row, split into
+// the fp16 hi and lo words of the tensor-core A operand.
+__device__ __forceinline__ void split_y(float x0, float x1, float o0, float o1, float ysc, uint32_t& hi,
+                                        uint32_t& lo)
+{
+    split_f16x2((x0 - o0) * ysc, (x1 - o1) * ysc, hi, lo);
 }
 
 // Z[rows][Np] = (Xc - o)[rows][D] * MT[D][Np] on the tensor cores with a
@@ -195,10 +203,11 @@ __device__ __forceinline__ uint32_t ldb(const uint32_t* p)
 // The dropped y_lo B_lo is below 2^-22 of a product; the power-of-two
 // scales keep every part inside the fp16 range and are undone exactly.
 // A warp takes a 16-row x 32-column tile (four n8 tiles of mma.m16n8k16);
-// its A fragments come straight from the row-major candidate rows (Dp apart,
-// zero beyond D), its B fragments from the pre-split rotation (shared
-// memory or, when it does not fit, global memory: the same arithmetic).
-// Rows at or beyond `rows` are computed from row rows-1 and discarded.
+// its A fragments are split here from the row-major candidate rows (Dp apart,
+// zero beyond D), its B fragments (one 64-bit load each, pair_word order)
+// come from the pre-split rotation (shared memory or, when it does not fit,
+// global memory: the same arithmetic).  Rows at or beyond `rows` are computed
+// from row rows-1 and discarded.
 template <bool B_SHARED>
 __device__ __forceinline__ void tile_gemm_f16x3(const float* __restrict__ Xc, int Dp, const float* __restrict__ o,
                                                 const uint32_t* __restrict__ Bh, const uint32_t* __restrict__ Bl,
@@ -215,47 +224,43 @@ __device__ __forceinline__ void tile_gemm_f16x3(const float* __restrict__ Xc, in
         const int ntn = min(4, (Np - nb) >> 3);
         const float* x0 = Xc + (size_t)min(r0, rows - 1) * Dp;
         const float* x1 = Xc + (size_t)min(r1, rows - 1) * Dp;
-        const uint32_t* bh = Bh + (size_t)(nb + g) * bws + t;
-        const uint32_t* bl = Bl + (size_t)(nb + g) * bws + t;
+        const uint32_t* bh = Bh + (size_t)(nb + g) * bws + 2 * t;
+        const uint32_t* bl = Bl + (size_t)(nb + g) * bws + 2 * t;
         float acc[4][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
         for (int ks = 0; ks < ksteps; ++ks) {
+            const int p = 8 * ks;
             // A elements (r, k0), (r, k0 + 1) and (r, k0 + 8), (r, k0 + 9);
             // Dp is a multiple of 4, so a pair is either inside the row or past it
             const int k0 = 16 * ks + 2 * t, k1 = k0 + 8;
-            float2 a00 = make_float2(0.f, 0.f), a10 = a00, a01 = a00, a11 = a00;
+            float2 u0 = make_float2(0.f, 0.f), v0 = u0, u1 = u0, v1 = u0, o0 = u0, o1 = u0;
             if (k0 < Dp) {
-                const float2 oo = *reinterpret_cast<const float2*>(o + k0);
-                const float2 u = *reinterpret_cast<const float2*>(x0 + k0);
-                const float2 v = *reinterpret_cast<const float2*>(x1 + k0);
-                a00 = make_float2((u.x - oo.x) * ysc, (u.y - oo.y) * ysc);
-                a10 = make_float2((v.x - oo.x) * ysc, (v.y - oo.y) * ysc);
+                o0 = *reinterpret_cast<const float2*>(o + k0);
+                u0 = *reinterpret_cast<const float2*>(x0 + k0);
+                v0 = *reinterpret_cast<const float2*>(x1 + k0);
             }
             if (k1 < Dp) {
-                const float2 oo = *reinterpret_cast<const float2*>(o + k1);
-                const float2 u = *reinterpret_cast<const float2*>(x0 + k1);
-                const float2 v = *reinterpret_cast<const float2*>(x1 + k1);
-                a01 = make_float2((u.x - oo.x) * ysc, (u.y - oo.y) * ysc);
-                a11 = make_float2((v.x - oo.x) * ysc, (v.y - oo.y) * ysc);
+                o1 = *reinterpret_cast<const float2*>(o + k1);
+                u1 = *reinterpret_cast<const float2*>(x0 + k1);
+                v1 = *reinterpret_cast<const float2*>(x1 + k1);
             }
             uint32_t ah[4], al[4];
-            split_f16x2(a00.x, a00.y, ah[0], al[0]);
-            split_f16x2(a10.x, a10.y, ah[1], al[1]);
-            split_f16x2(a01.x, a01.y, ah[2], al[2]);
-            split_f16x2(a11.x, a11.y, ah[3], al[3]);
-            const int p = 8 * ks;
+            split_y(u0.x, u0.y, o0.x, o0.y, ysc, ah[0], al[0]);
+            split_y(v0.x, v0.y, o0.x, o0.y, ysc, ah[1], al[1]);
+            split_y(u1.x, u1.y, o1.x, o1.y, ysc, ah[2], al[2]);
+            split_y(v1.x, v1.y, o1.x, o1.y, ysc, ah[3], al[3]);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (j < ntn) {
                     const size_t cj = (size_t)(8 * j) * bws + p;
-                    const uint32_t h0 = ldb<B_SHARED>(bh + cj), h1 = ldb<B_SHARED>(bh + cj + 4);
-                    const uint32_t l0 = ldb<B_SHARED>(bl + cj), l1 = ldb<B_SHARED>(bl + cj + 4);
-                    mma_f16(acc[j], al, h0, h1);
-                    mma_f16(acc[j], ah, l0, l1);
-                    mma_f16(acc[j], ah, h0, h1);
+                    const uint2 hb = ldb2<B_SHARED>(bh + cj);
+                    const uint2 lb = ldb2<B_SHARED>(bl + cj);
+                    mma_f16(acc[j], al, hb.x, hb.y);
+                    mma_f16(acc[j], ah, lb.x, lb.y);
+                    mma_f16(acc[j], ah, hb.x, hb.y);
                 }
             }
         }
