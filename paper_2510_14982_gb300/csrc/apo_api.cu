@@ -206,7 +206,6 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
 
     const int Dp = (D + 3) & ~3;
     const int Np = (D + 15) & ~15;
-    const int Kp = (D + 15) & ~15;
     const int bws = split_words(D);
     // Host image of every device array, laid out in one allocation.
     std::vector<std::pair<size_t, std::vector<unsigned char>>> pieces;
