@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kTThreads) gemm_bf16_tc_kernel(GemmArgs g, boo
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" : : "r"(tmem), "r"(kTN) : "memory");
-    if (!ok && tid == 0) atomicExch(err, 1);
+    if (!ok && tid == 0) atomicCAS(err, 0, 4 /* APO_ERR_TIMEOUT */);
 }
 
 // C(m, n) = sum_k A(m, k) B(k, n), A(m, k) = TA ? A[k lda + m] : A[m lda + k],

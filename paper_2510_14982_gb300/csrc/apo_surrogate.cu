@@ -287,6 +287,15 @@ extern "C" apo_status apo_mlp_gradients(apo_mlp* M, const float* d_X, const floa
     if (rc == APO_OK) rc = mlp_backward_rows(M, n, 0);
     if (rc != APO_OK) return rc;
     SUR_CUDA(cudaDeviceSynchronize());
+    if (int* status = device_status_word()) {   // a GEMM wait that ran out
+        int h = 0;
+        SUR_CUDA(cudaMemcpy(&h, status, 4, cudaMemcpyDeviceToHost));
+        if (h != 0) {
+            cudaMemset(status, 0, 4);
+            apo::set_last_error("a device-side wait exceeded its limit");
+            return (apo_status)h;
+        }
+    }
     std::vector<float> tmp((size_t)M->Kp * kH);
     if (gW1) {
         SUR_CUDA(cudaMemcpy(tmp.data(), M->gW1, tmp.size() * 4, cudaMemcpyDeviceToHost));
@@ -896,6 +905,10 @@ extern "C" apo_status apo_run_surrogate(const apo_problem* P, const apo_params* 
     apo_mlp_destroy(M);
     int h = 0;
     cudaMemcpy(&h, status, 4, cudaMemcpyDeviceToHost);
-    if (h != 0) { apo::set_last_error("a device-side wait exceeded its limit"); return (apo_status)h; }
+    if (h != 0) {
+        cudaMemset(status, 0, 4);
+        apo::set_last_error("a device-side wait exceeded its limit");
+        return (apo_status)h;
+    }
     return APO_OK;
 }
