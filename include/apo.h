@@ -286,6 +286,15 @@ apo_status apo_run_surrogate(const apo_problem* prob, const apo_params* params, 
 apo_status apo_surrogate_candidates(const apo_problem* prob, const apo_params* params, int iter, int k,
                                     void* stream, const float* d_X, const float* d_F, float* d_Xcand);
 
+/* Test hook of the grid barrier that the cooperative iteration loop uses
+ * between its phases: ctas_launched CTAs (at most one per SM) each pass
+ * `rounds` barriers of a run that expects ctas_expected CTAs.  Returns
+ * APO_OK when launched == expected; with fewer CTAs the first wait runs out
+ * after its limit (4 s), the kernel records APO_ERR_TIMEOUT in the device
+ * status word and returns, and the call reports (and clears) that status;
+ * the context stays usable.  No counterpart in the paper.  Synchronous. */
+apo_status apo_barrier_selftest(int ctas_launched, int ctas_expected, int rounds, void* stream);
+
 /* Test hook: the device Philox4x32-10 on n counters d_ctr [n*4] with key
  * (key0, key1) into d_out [n*4].  Stream-ordered. */
 apo_status apo_philox4x32_10(const uint32_t* d_ctr, uint32_t key0, uint32_t key1, int n,

@@ -32,7 +32,7 @@ EXPORTS = ("apo_problem_create", "apo_problem_destroy", "apo_problem_dim", "apo_
            "apo_step", "apo_evaluate", "apo_clamp_eval_select", "apo_histogram_u8",
            "apo_mlp_create", "apo_mlp_destroy", "apo_mlp_set_params", "apo_mlp_get_params", "apo_mlp_forward",
            "apo_mlp_gradients", "apo_mlp_train",
-           "apo_run_surrogate", "apo_surrogate_candidates",
+           "apo_run_surrogate", "apo_surrogate_candidates", "apo_barrier_selftest",
            "apo_philox4x32_10", "apo_set_timing_events", "apo_status_string", "apo_last_error")
 
 
@@ -102,6 +102,8 @@ for _f in ("apo_mlp_create", "apo_mlp_set_params", "apo_mlp_get_params", "apo_ml
     getattr(_lib, _f).restype = C.c_int
 _lib.apo_surrogate_candidates.argtypes = [_P, C.POINTER(apo_params), C.c_int, C.c_int, _P, _P, _P, _P]
 _lib.apo_surrogate_candidates.restype = C.c_int
+_lib.apo_barrier_selftest.argtypes = [C.c_int, C.c_int, C.c_int, _P]
+_lib.apo_barrier_selftest.restype = C.c_int
 _lib.apo_run_surrogate.argtypes = [_P, C.POINTER(apo_params), C.POINTER(apo_surrogate_params), _P, _FP,
                                    C.POINTER(C.c_double), _FP, C.POINTER(apo_surrogate_stats)]
 _lib.apo_run_surrogate.restype = C.c_int
@@ -388,6 +390,12 @@ def apo_surrogate_candidates(prob: Problem, params: apo_params, it: int, k: int,
     protozoon into d_Xcand [ps, k, D], rank-major."""
     _check(_lib.apo_surrogate_candidates(prob.handle, C.byref(params), int(it), int(k), _stream(stream), _dptr(d_X),
                                          _dptr(d_F), _dptr(d_Xcand)), "apo_surrogate_candidates")
+
+
+def apo_barrier_selftest(launched: int, expected: int, rounds: int = 1, stream=None) -> int:
+    """apo_barrier_selftest (test hook): the raw status code (0 = APO_OK,
+    4 = APO_ERR_TIMEOUT); does not raise."""
+    return int(_lib.apo_barrier_selftest(int(launched), int(expected), int(rounds), _stream(stream)))
 
 
 def raw_lib():

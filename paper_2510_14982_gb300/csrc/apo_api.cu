@@ -1052,6 +1052,32 @@ extern "C" apo_status apo_set_timing_events(void* before, void* after)
     return APO_OK;
 }
 
+extern "C" apo_status apo_barrier_selftest(int ctas_launched, int ctas_expected, int rounds, void* stream)
+{
+    if (ctas_launched < 1 || ctas_expected < 1 || ctas_launched > ctas_expected || ctas_expected > 1024 ||
+        rounds < 1 || rounds > 100000) {
+        set_err("barrier self-test: 1 <= launched <= expected <= 1024, 1 <= rounds <= 100000");
+        return APO_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    APO_CUDA(cudaGetDevice(&dev));
+    int* status = device_status(dev);
+    if (!status) { set_err("status word allocation failed"); return APO_ERR_OOM; }
+    // every launched CTA must be resident at once for the barrier to complete
+    int sms = 0;
+    APO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (ctas_launched > sms) { set_err("barrier self-test: at most one CTA per SM"); return APO_ERR_INVALID_ARG; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned* bar = nullptr;
+    APO_CUDA(cudaMalloc(&bar, 256));
+    cudaError_t e = cudaMemsetAsync(bar, 0, 256, st);
+    if (e == cudaSuccess) e = launch_barrier_test(bar, ctas_launched, ctas_expected, rounds, status, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(bar);
+    if (e != cudaSuccess) { set_err("barrier self-test launch failed: %s", cudaGetErrorString(e)); return APO_ERR_CUDA; }
+    return read_device_status(dev);
+}
+
 extern "C" apo_status apo_philox4x32_10(const uint32_t* d_ctr, uint32_t key0, uint32_t key1, int n, uint32_t* d_out,
                                         void* stream)
 {

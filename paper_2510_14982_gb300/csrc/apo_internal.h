@@ -55,6 +55,10 @@ apo_status sched_tables(int ps, int pdr_form, int T, const uint32_t** thr_dr, co
 // Process-wide device status word (first device-side error wins).
 int* device_status_word();
 
+// Barrier self-test launch (see apo_barrier_selftest).
+cudaError_t launch_barrier_test(unsigned* d_bar, int launched, int expected, int rounds, int* status,
+                                cudaStream_t st);
+
 // Sets the text that apo_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
 

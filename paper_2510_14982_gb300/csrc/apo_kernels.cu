@@ -753,6 +753,24 @@ cudaError_t launch_eval(const ApoRun* d_run, int n, const float* d_X, void* d_F,
     return launch_eval_t<float, 1>(d_run, n, d_X, d_F, select, d_Xsel, d_Fsel, smem, st);
 }
 
+// Barrier self-test: `launched` CTAs each pass `rounds` grid barriers of a
+// run that expects `expected` CTAs.  With launched == expected every barrier
+// completes; with fewer, the first wait runs out after its limit, sets
+// APO_ERR_TIMEOUT and the run's abort flag, and every CTA returns.
+__global__ void barrier_test_kernel(unsigned* bar, int expected, int rounds, int* status)
+{
+    __shared__ int s_flag;
+    unsigned gen = 0;
+    for (int i = 0; i < rounds; ++i)
+        if (!run_barrier(bar, expected, gen, status, &s_flag)) return;
+}
+
+cudaError_t launch_barrier_test(unsigned* d_bar, int launched, int expected, int rounds, int* status, cudaStream_t st)
+{
+    barrier_test_kernel<<<launched, 64, 0, st>>>(d_bar, expected, rounds, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_philox(const uint32_t* d_ctr, uint32_t k0, uint32_t k1, int n, uint32_t* d_out,
                           cudaStream_t st)
 {
