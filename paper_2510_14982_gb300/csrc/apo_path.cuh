@@ -95,71 +95,6 @@ __device__ __forceinline__ void load_constants(const ApoRun& R, const Smem<FitT>
 }
 
 // ------------------------------------------------------------ evaluation
-// 16-byte shared-memory load through an explicit shared-window address.
-__device__ __forceinline__ float4 lds4(uint32_t addr)
-{
-    float4 v;
-    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
-    return v;
-}
-
-// Z[rows][Np] = Y[rows][Dp] * MT[Dp][Np] with Y stored transposed (YT[k][row],
-// row stride CH) and both operands zero padded beyond D.  FP32 FMA (the
-// composition's components, whose rotations stay in global memory).  A warp
-// computes an 8-row x 128-column tile, lane L the columns 4L..4L+3 of the 8
-// rows: per k the 8 row values are two broadcast 16-byte loads shared by the
-// whole warp and the columns one 16-byte load per lane (through L1).
-template <int TR>
-__device__ __forceinline__ void tile_gemm_t(const float* __restrict__ YT, const float* __restrict__ MT,
-                                            float* __restrict__ Z, int rows, int Dp, int Np, int CH)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int rt = (rows + TR - 1) / TR, ct = (Np + 127) >> 7;
-    const uint32_t yt_s = (uint32_t)__cvta_generic_to_shared(YT);
-    for (int tile = warp; tile < rt * ct; tile += nw) {
-        const int tr = tile / ct, tc = tile - tr * ct;
-        const int rb = TR * tr, c = 128 * tc + 4 * lane;
-        const bool col_ok = c < Np;
-        float acc[TR][4];
-#pragma unroll
-        for (int i = 0; i < TR; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-#pragma unroll 2
-        for (int k = 0; k < Dp; ++k) {
-            const uint32_t ya = yt_s + 4u * (uint32_t)(k * CH + rb);
-            const float4 a0 = lds4(ya);
-            const float4 a1 = TR == 8 ? lds4(ya + 16u) : make_float4(0.f, 0.f, 0.f, 0.f);
-            float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (col_ok) b = __ldg(reinterpret_cast<const float4*>(MT + (size_t)k * Np + c));
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-#pragma unroll
-            for (int i = 0; i < TR; ++i) {
-                acc[i][0] = fmaf(av[i], b.x, acc[i][0]);
-                acc[i][1] = fmaf(av[i], b.y, acc[i][1]);
-                acc[i][2] = fmaf(av[i], b.z, acc[i][2]);
-                acc[i][3] = fmaf(av[i], b.w, acc[i][3]);
-            }
-        }
-        if (col_ok) {
-#pragma unroll
-            for (int i = 0; i < TR; ++i)
-                if (rb + i < rows)
-                    *reinterpret_cast<float4*>(Z + (size_t)(rb + i) * Np + c) =
-                        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-        }
-    }
-}
-
-// 8-row tiles when they keep every warp busy, 4-row tiles otherwise.
-__device__ __forceinline__ void tile_gemm(const float* __restrict__ YT, const float* __restrict__ MT,
-                                          float* __restrict__ Z, int rows, int Dp, int Np, int CH)
-{
-    const int nw = blockDim.x >> 5, ct = (Np + 127) >> 7;
-    if (((rows + 7) >> 3) * ct >= nw) tile_gemm_t<8>(YT, MT, Z, rows, Dp, Np, CH);
-    else tile_gemm_t<4>(YT, MT, Z, rows, Dp, Np, CH);
-}
-
 // ------------------------------------------------ tensor-core rotation
 // (a, b) -> fp16 pairs hi = round(a, b), lo = round((a, b) - hi); hi + lo
 // carries 22 significant bits.  The lower half holds a.
@@ -381,26 +316,28 @@ __device__ __forceinline__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S,
     for (int c = 0; c < P.ncomp; ++c) {
         const DevComp& C = P.comp[c];
         const float* o = (c == 0) ? S.o : C.o;
-        // YT[d][row] = x - o (zero beyond D)
-        for (int i = threadIdx.x; i < CH * Dp; i += blockDim.x) {
-            const int d = i / CH, row = i - d * CH;
-            S.Yc[i] = (d < D && row < rows) ? S.Xc[(size_t)row * Dp + d] - o[d] : 0.f;
+        if (C.Bh) {
+            // a rotated component of the composition: tensor-core rotation,
+            // its split rotation read from global memory
+            tile_gemm_f16x3<false>(S.Xc, Dp, o, C.Bh, C.Bl, P.bws, C.ysc, C.zsc, S.Zc, Np, rows, D);
+        } else {
+            // no rotation: YT[d][row] = x - o (zero beyond D)
+            for (int i = threadIdx.x; i < CH * Dp; i += blockDim.x) {
+                const int d = i / CH, row = i - d * CH;
+                S.Yc[i] = (d < D && row < rows) ? S.Xc[(size_t)row * Dp + d] - o[d] : 0.f;
+            }
         }
         __syncthreads();
-        if (C.MT) {
-            tile_gemm(S.Yc, C.MT, S.Zc, rows, Dp, Np, CH);
-            __syncthreads();
-        }
         const float* ew = (c == 0) ? S.ew : C.ew;
         for (int row = warp; row < rows; row += nw) {
-            const float v = C.MT ? seg_value(S.Zc + (size_t)row * Np, 1, C, ew, D)
+            const float v = C.Bh ? seg_value(S.Zc + (size_t)row * Np, 1, C, ew, D)
                                  : seg_value(S.Yc + row, CH, C, ew, D);
             if (P.ncomp == 1) {
                 if (lane == 0) S.rowF[row] = (FitT)v;
             } else {
                 float d2 = 0.f;
                 for (int d = lane; d < D; d += 32) {
-                    const float y = S.Yc[(size_t)d * CH + row];
+                    const float y = S.Xc[(size_t)row * Dp + d] - o[d];
                     d2 = fmaf(y, y, d2);
                 }
                 d2 = warp_sum(d2);

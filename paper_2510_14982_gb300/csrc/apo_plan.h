@@ -33,10 +33,10 @@ inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool
     L.mt_smem = mt_smem;
     L.chunk = chunk > 0 ? chunk : (grid ? kGridChunk : kChunk);
     L.threads = grid ? kGridThreads : kThreads;
-    // a single rotated component is evaluated on the tensor cores: its split
-    // rotation (Bh, Bl) may live in shared memory and no transposed copy of
-    // the candidates is needed
-    const bool rot1 = P->ncomp == 1 && P->dev.comp[0].MT != nullptr;
+    // rotated components are evaluated on the tensor cores from the row-major
+    // candidates; only an unrotated one needs the transposed copy Yc
+    bool any_plain = false;
+    for (int c = 0; c < P->ncomp; ++c) any_plain = any_plain || P->dev.comp[c].MT == nullptr;
     const size_t ch = (size_t)L.chunk;
     size_t off = 0;
     auto take = [&](size_t bytes) -> uint32_t {
@@ -59,7 +59,7 @@ inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool
     L.ew = take(Dp * 4);
     L.Xc = take(ch * Dp * 4);
     L.Xo = take(grid ? 0 : ch * Dp * 4);                // grid mode copies no unchanged rows
-    L.Yc = take(rot1 ? 0 : ch * Dp * 4);               // transposed: [Dp][chunk]
+    L.Yc = take(any_plain ? ch * Dp * 4 : 0);          // transposed: [Dp][chunk]
     L.Zc = take(P->any_rot ? ch * Np * 4 : 0);          // [chunk][Np]
     L.rowF = take(2 * ch * fsz);   // new fitness | old fitness of the chunk rows
     L.compG = take(P->ncomp > 1 ? ch * kMaxComp * 4 : 0);
