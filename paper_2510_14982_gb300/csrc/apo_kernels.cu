@@ -5,8 +5,9 @@
 // the whole device-side iteration loop of one optimisation run:
 //   sort (F, previous rank) -> [Dr_index, precomputed by dr_kernel]
 //   -> candidate generation, one warp per protozoon (Eq. 1-10, 12-13)
-//   -> bound clamp -> evaluation (z = M (x - o) as a shared-memory tile GEMM,
-//      then the objective epilogue) -> greedy replacement -> barrier.
+//   -> bound clamp -> evaluation (z = M (x - o) as a three-term fp16 tensor
+//      core product per chunk, then the objective epilogue) -> greedy
+//      replacement -> barrier.
 // In resident mode the population, its fitness and the rotation live in
 // shared memory; in grid mode the population lives in global memory (L2) and
 // is double buffered so that every candidate reads the start-of-iteration

@@ -480,19 +480,19 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
 
     // per-dimension draws and the mask (independent of the gathered rows,
     // overlapping their latency)
+    // branch-free, so that the QPL independent Philox chains of a lane
+    // interleave (a lane past D computes a draw it then discards)
     uint32_t A[2 * QPL], B[2 * QPL];
     uint32_t valid = 0;
 #pragma unroll
     for (int j = 0; j < QPL; ++j) {
         const int q = lane + 32 * j;
-        if (2 * q < D) {
-            const uint4 w = philox((uint32_t)t, (uint32_t)r, (uint32_t)q, kSlotDim | cs, seed, run);
-            A[2 * j] = w.x; B[2 * j] = w.y; A[2 * j + 1] = w.z; B[2 * j + 1] = w.w;
-            valid |= 1u << (2 * j);
-            if (2 * q + 1 < D) valid |= 1u << (2 * j + 1);
-        } else {
-            A[2 * j] = B[2 * j] = A[2 * j + 1] = B[2 * j + 1] = 0u;
-        }
+        const uint4 w = philox((uint32_t)t, (uint32_t)r, (uint32_t)q, kSlotDim | cs, seed, run);
+        const bool v0 = 2 * q < D, v1 = 2 * q + 1 < D;
+        A[2 * j] = v0 ? w.x : 0u; B[2 * j] = v0 ? w.y : 0u;
+        A[2 * j + 1] = v0 ? w.z : 0u; B[2 * j + 1] = v0 ? w.w : 0u;
+        valid |= (v0 ? 1u : 0u) << (2 * j);
+        valid |= (v1 ? 1u : 0u) << (2 * j + 1);
     }
     uint32_t mask = 0;
     if (mode == kReproduction) {
@@ -550,15 +550,17 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     const float rho = u01(sc.w);
     const float nsc = R.nsc[t];
 
-    float* xc = S.Xc + (size_t)row * Dp;
-    float* xo = S.Xo + (size_t)row * Dp;
+    float2* xc = reinterpret_cast<float2*>(S.Xc + (size_t)row * Dp);
+    float2* xo = reinterpret_cast<float2*>(S.Xo + (size_t)row * Dp);
 #pragma unroll
     for (int j = 0; j < QPL; ++j) {
         const int q = lane + 32 * j;
+        float out[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int d = 2 * q + e;
             const int sl = 2 * j + e;
+            out[e] = 0.f;
             if (d < D) {
                 const float lb = S.lb[d], ub = S.ub[d];
                 const bool mk = (mask >> sl) & 1u;
@@ -576,12 +578,15 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
                         x = x0 + ff * (xnear - x0 + acc[sl] * inv_np);          // Eq. 8
                     }
                 }
-                xc[d] = fminf(fmaxf(x, lb), ub);
-                if (keep_old) xo[d] = x0;
-            } else if (d < Dp) {
-                xc[d] = 0.f;
-                if (keep_old) xo[d] = 0.f;
+                out[e] = fminf(fmaxf(x, lb), ub);
             }
+        }
+        // Dp is a multiple of 4, so a pair starting below Dp lies inside the
+        // row; the padding past D is written as zeros
+        if (2 * q < Dp) {
+            xc[q] = make_float2(out[0], out[1]);
+            if (keep_old)
+                xo[q] = make_float2(2 * q < D ? xi[2 * j] : 0.f, 2 * q + 1 < D ? xi[2 * j + 1] : 0.f);
         }
     }
 }
