@@ -418,15 +418,26 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     const int lane = threadIdx.x & 31;
     const int D = R.prob.D, Dp = R.prob.Dp, ps = R.ps, np = R.np;
     const uint32_t seed = R.seed, run = R.run;
-    // lane 0: SCAL, lane 1: SCAL2, lane 2 + k: PAIR k
-    uint32_t jslot = kSlotPair | cs, jd = (uint32_t)(lane - 2);
-    if (lane == 0) { jslot = kSlotScal | cs; jd = kAll; }
-    if (lane == 1) { jslot = kSlotScal2 | cs; jd = kAll; }
+    // Per-protozoon draws, from lanes jb + u: u = 0 SCAL, u = 1 SCAL2,
+    // u = 2 + k PAIR k.  The last per-dimension call of a lane covers pairs
+    // q = lane + 32 (QPL - 1), of which only q < ceil(D / 2) exist; when at
+    // least three lanes are left over there (jb <= 29) the per-protozoon
+    // draws take those lanes and the call does both jobs, else they get a
+    // call of their own (jb = 0).  Every draw keeps its own counter, so the
+    // values do not depend on this placement.
+    const int jb_free = max(0, ((D + 1) >> 1) - 32 * (QPL - 1));   // in [0, 32]
+    const bool merged = jb_free <= 29;
+    const int jb = merged ? jb_free : 0;
+    const int u = lane - jb;
+    uint32_t jslot = kSlotPair | cs, jd = (uint32_t)(u - 2);
+    if (u == 0) { jslot = kSlotScal | cs; jd = kAll; }
+    if (u == 1) { jslot = kSlotScal2 | cs; jd = kAll; }
+    if (u < 0) { jslot = kSlotDim | cs; jd = (uint32_t)(lane + 32 * (QPL - 1)); }
     const uint4 jw = philox((uint32_t)t, (uint32_t)r, jd, jslot, seed, run);
     uint4 sc, sc2;
-    sc.x = __shfl_sync(0xffffffffu, jw.x, 0); sc.y = __shfl_sync(0xffffffffu, jw.y, 0);
-    sc.z = __shfl_sync(0xffffffffu, jw.z, 0); sc.w = __shfl_sync(0xffffffffu, jw.w, 0);
-    sc2.x = __shfl_sync(0xffffffffu, jw.x, 1); sc2.y = __shfl_sync(0xffffffffu, jw.y, 1);
+    sc.x = __shfl_sync(0xffffffffu, jw.x, jb); sc.y = __shfl_sync(0xffffffffu, jw.y, jb);
+    sc.z = __shfl_sync(0xffffffffu, jw.z, jb); sc.w = __shfl_sync(0xffffffffu, jw.w, jb);
+    sc2.x = __shfl_sync(0xffffffffu, jw.x, jb + 1); sc2.y = __shfl_sync(0xffffffffu, jw.y, jb + 1);
     const int W = (ps + 31) >> 5;
     const bool in_dr = (R.drmask[(size_t)t * W + (r >> 5)] >> (r & 31)) & 1u;
     const uint32_t mm = m24p1(sc.x);
@@ -444,7 +455,7 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     uint32_t ej = ei, ea = ei, eb = ei;
     if (mode == kAutotrophic) {
         ej = perm[idx_draw(sc2.y, (uint32_t)ps)];
-        const uint32_t p0 = __shfl_sync(0xffffffffu, jw.x, 2), p1 = __shfl_sync(0xffffffffu, jw.y, 2);
+        const uint32_t p0 = __shfl_sync(0xffffffffu, jw.x, jb + 2), p1 = __shfl_sync(0xffffffffu, jw.y, jb + 2);
         ea = perm[idx_draw(p0, (uint32_t)ps)];
         eb = perm[idx_draw(p1, (uint32_t)ps)];
     } else if (mode == kHeterotrophic) {
@@ -487,7 +498,9 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
 #pragma unroll
     for (int j = 0; j < QPL; ++j) {
         const int q = lane + 32 * j;
-        const uint4 w = philox((uint32_t)t, (uint32_t)r, (uint32_t)q, kSlotDim | cs, seed, run);
+        uint4 w;
+        if (j == QPL - 1 && merged) w = jw;   // lanes >= jb hold no pair here (2 q >= D)
+        else w = philox((uint32_t)t, (uint32_t)r, (uint32_t)q, kSlotDim | cs, seed, run);
         const bool v0 = 2 * q < D, v1 = 2 * q + 1 < D;
         A[2 * j] = v0 ? w.x : 0u; B[2 * j] = v0 ? w.y : 0u;
         A[2 * j + 1] = v0 ? w.z : 0u; B[2 * j + 1] = v0 ? w.w : 0u;
@@ -512,9 +525,9 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
         for (int k = 2; k <= np; ++k) {
             if (mode == kAutotrophic) {
                 uint32_t p0, p1;
-                if (k + 1 < 32) {
-                    p0 = __shfl_sync(0xffffffffu, jw.x, k + 1);
-                    p1 = __shfl_sync(0xffffffffu, jw.y, k + 1);
+                if (jb + k + 1 < 32) {
+                    p0 = __shfl_sync(0xffffffffu, jw.x, jb + k + 1);
+                    p1 = __shfl_sync(0xffffffffu, jw.y, jb + k + 1);
                 } else {
                     const uint4 pr = philox((uint32_t)t, (uint32_t)r, (uint32_t)(k - 1), kSlotPair | cs, seed, run);
                     p0 = pr.x;

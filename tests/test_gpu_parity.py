@@ -126,6 +126,14 @@ STEP_CASES = [
     ("d200_ps256", lambda: inputs.shifted_rotated(inputs.OBJ_RASTRIGIN, 200, 6), 256, 2, 300, {}),
     ("composition20_ps64", lambda: inputs.composition(D=20, seed=9), 64, 4, 300, {}),
     ("odd_d1", lambda: inputs.shifted_rotated(inputs.OBJ_ELLIPTIC, 1, 7), 40, 2, 10, {}),
+    # placement of the per-protozoon draws: a call of their own when fewer
+    # than three lanes of the last per-dimension call are free (D 64, D 126),
+    # a last call with no pair at all (D 150), pair draws past lane 31 (np 16)
+    ("d64_own_scalar_call", lambda: inputs.shifted_rotated(inputs.OBJ_RASTRIGIN, 64, 8), 128, 3, 100, {}),
+    ("d126_np3_own_scalar_call", lambda: inputs.shifted_rotated(inputs.OBJ_HYBRID, 126, 9), 200, 4, 100,
+     dict(np_=3)),
+    ("d150_free_last_call", lambda: inputs.shifted_rotated(inputs.OBJ_ELLIPTIC, 150, 10), 128, 2, 100, {}),
+    ("d100_np16", lambda: inputs.shifted_rotated(inputs.OBJ_RASTRIGIN, 100, 11), 256, 3, 100, dict(np_=16)),
 ]
 
 
