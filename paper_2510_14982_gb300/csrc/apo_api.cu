@@ -223,8 +223,8 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
     for (int d = 0; d < D; ++d) { lbf[d] = (float)lb[d]; ubf[d] = (float)ub[d]; }
     const size_t off_lb = add(lbf.data(), Dp * 4), off_ub = add(ubf.data(), Dp * 4);
     size_t off_o[kMaxComp] = {}, off_mt[kMaxComp] = {}, off_ew[kMaxComp] = {}, off_bh[kMaxComp] = {},
-           off_bl[kMaxComp] = {};
-    bool has_mt[kMaxComp] = {};
+           off_bl[kMaxComp] = {}, off_th[kMaxComp] = {}, off_tl[kMaxComp] = {};
+    bool has_mt[kMaxComp] = {}, has_tc[kMaxComp] = {};
     DevComp comps[kMaxComp] = {};
     int any_rot = 0;
     for (int k = 0; k < ncomp; ++k) {
@@ -260,7 +260,11 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
                 ymax = std::max(ymax, std::max(std::fabs((double)ubf[d] - (double)o[d]),
                                                std::fabs((double)lbf[d] - (double)o[d])));
             const float msc = pow2_scale(mmax, 12), ysc = pow2_scale(ymax, 10);
+            // A single component with D <= kTcM also gets the parts in the
+            // canonical UMMA layout (rows n, columns k; Np x Np each).
+            const bool tc = ncomp == 1 && Np <= kTcM;
             std::vector<uint32_t> bh((size_t)Np * bws, 0u), bl((size_t)Np * bws, 0u);
+            std::vector<uint16_t> th(tc ? (size_t)Np * Np : 0, 0), tl(tc ? (size_t)Np * Np : 0, 0);
             for (int n = 0; n < D; ++n)
                 for (int kk = 0; kk < D; ++kk) {
                     const float v = mt[(size_t)kk * Np + n] * msc;
@@ -269,9 +273,18 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
                     const uint32_t sh = (kk & 1) ? 16u : 0u;
                     bh[(size_t)n * bws + pair_word(kk / 2)] |= (uint32_t)half_bits(hh) << sh;
                     bl[(size_t)n * bws + pair_word(kk / 2)] |= (uint32_t)half_bits(ll) << sh;
+                    if (tc) {
+                        th[umma_off(n, kk, Np) / 2] = half_bits(hh);
+                        tl[umma_off(n, kk, Np) / 2] = half_bits(ll);
+                    }
                 }
             off_bh[k] = add(bh.data(), bh.size() * 4);
             off_bl[k] = add(bl.data(), bl.size() * 4);
+            if (tc) {
+                off_th[k] = add(th.data(), th.size() * 2);
+                off_tl[k] = add(tl.data(), tl.size() * 2);
+                has_tc[k] = true;
+            }
             comps[k].ysc = ysc;
             comps[k].zsc = 1.f / (ysc * msc);   // a power of two: exact
         }
@@ -374,6 +387,8 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
         dp.comp[k].MT = has_mt[k] ? reinterpret_cast<const float*>(base + off_mt[k]) : nullptr;
         dp.comp[k].Bh = has_mt[k] ? reinterpret_cast<const uint32_t*>(base + off_bh[k]) : nullptr;
         dp.comp[k].Bl = has_mt[k] ? reinterpret_cast<const uint32_t*>(base + off_bl[k]) : nullptr;
+        dp.comp[k].Th = has_tc[k] ? reinterpret_cast<const uint4*>(base + off_th[k]) : nullptr;
+        dp.comp[k].Tl = has_tc[k] ? reinterpret_cast<const uint4*>(base + off_tl[k]) : nullptr;
         dp.comp[k].ew = reinterpret_cast<const float*>(base + off_ew[k]);
     }
     if (kind == APO_OBJ_OTSU) {

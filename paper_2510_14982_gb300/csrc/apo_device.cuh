@@ -53,7 +53,12 @@ struct DevComp {
     // order, zero padded.
     const uint32_t* Bh;
     const uint32_t* Bl;
-    float ysc;           // power of two bringing |x - o| over the box near 2^14
+    // The same fp16 parts in the canonical K-major UMMA layout (umma_off,
+    // Np rows n x Np columns k each), for the tcgen05 rotation of the grid
+    // kernel; only for a single component with D <= kTcM, else nullptr.
+    const uint4* Th;
+    const uint4* Tl;
+    float ysc;           // power of two bringing |x - o| over the box below 2^10
     float zsc;           // 1 / (ysc * msc): z = zsc * (ysc (x - o)) . B
     const float* ew;     // [Dp] elliptic weights of the first segment
     int s1, s2;
@@ -89,6 +94,21 @@ __host__ __device__ __forceinline__ int split_words(int D)
     return (h % 16 == 8) ? h : h + 8;
 }
 
+// The tcgen05 rotation of the cooperative grid kernel: UMMA M = kTcM output
+// dimensions (the rotation rows, D <= kTcM), N = kTcN candidate rows of a
+// chunk (the accumulator's TMEM columns).
+constexpr int kTcM = 128;
+constexpr int kTcN = 64;
+
+// Byte offset of element (r, k) of a K-major operand with Kt columns (a
+// multiple of 16) in the canonical UMMA layout without swizzle: core
+// matrices of 8 rows x 16 bytes, K-adjacent ones 128 bytes apart, 8-row
+// groups Kt * 16 bytes apart.
+__host__ __device__ __forceinline__ uint32_t umma_off(int r, int k, int Kt)
+{
+    return (uint32_t)((r >> 3) * (Kt * 16) + (k >> 3) * 128 + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
 // Packed index of the bin range [a, b] (0 <= a <= b <= 255) in the Otsu term table.
 __host__ __device__ __forceinline__ int otsu_tab_index(int a, int b)
 {
@@ -101,10 +121,11 @@ struct SmemPlan {
     int ps_pad;          // power of two >= ps
     int resident;        // population lives in shared memory
     int mt_smem;         // rotation of component 0 lives in shared memory
+    int tc;              // grid kernel rotation on tcgen05 (operands TA, TY)
     int chunk;           // candidate rows evaluated together
     int threads;         // CTA size the plan was made for
     uint32_t X0, X1, F0, F1, perm0, perm1, keys, MT, o, lb, ub, ew, Xc, Xo, Yc, Zc,
-        rowF, compG, compA, P0, P1, otsu, red, nloc, total;
+        rowF, compG, compA, P0, P1, otsu, red, nloc, TA, TY, total;
 };
 
 struct ApoRun {

@@ -17,6 +17,7 @@
 #include "apo_device.cuh"
 #include "apo_internal.h"
 #include "apo_path.cuh"
+#include "apo_umma.cuh"
 
 namespace apo {
 
@@ -391,7 +392,8 @@ __device__ __forceinline__ void block_scan_inclusive(int* a, int n, int* wsum)
 }
 
 template <typename FitT, int QPL>
-__device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned char* smem, int* status, int* s_flag)
+__device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned char* smem, int* status, int* s_flag,
+                                         TcState& tcs)
 {
     using KO = KeyOf<FitT>;
     using KT = typename KO::T;
@@ -403,6 +405,20 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
     const int CH = L.chunk;
     const Smem<FitT> S = carve<FitT>(smem, L);
     unsigned bgen = 0;
+    // chunk evaluation: tcgen05 rotation (plan.tc) or the general path; a
+    // tensor-core wait that runs out aborts the run (false for every thread)
+    auto evaluate = [&](int rows) -> bool {
+        if (!L.tc) {
+            eval_chunk<FitT>(R, S, rows);
+            return true;
+        }
+        if (eval_chunk_tc<FitT>(R, S, rows, tcs)) return true;
+        if (tid == 0) {
+            set_status(status, 4 /* APO_ERR_TIMEOUT */);
+            atomicExch(&R.bar[2], 1u);
+        }
+        return false;
+    };
 
     load_constants<FitT>(R, S);
     float* Xs[2] = {R.X[0], R.X[1]};
@@ -432,7 +448,7 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
             const int rows = min(CH, nown - c0);
             for (int row = warp; row < rows; row += nw) gen_init_row<FitT, QPL>(R, S, pos_of(c0 + row), row);
             __syncthreads();
-            eval_chunk<FitT>(R, S, rows);
+            if (!evaluate(rows)) return;
             for (int row = warp; row < rows; row += nw) {
                 const int p = pos_of(c0 + row);
                 float* dst = Xs[0] + (size_t)p * Dp;
@@ -534,7 +550,7 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
             for (int row = warp; row < rows; row += nw)
                 gen_step_row<FitT, QPL>(R, S, Xs[0], Xs[1], Fs[cur], perm, false, false, t, pos_of(c0 + row), row);
             __syncthreads();
-            eval_chunk<FitT>(R, S, rows);
+            if (!evaluate(rows)) return;
             // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i).
             // An accepted row goes to the slot's other buffer (nobody reads it
             // in this iteration) and flips the slot's buffer bit; a rejected
@@ -589,7 +605,12 @@ __global__ void __launch_bounds__(kGridThreads, 1) grid_kernel(const ApoRun* __r
     if (run >= n_runs) return;
     copy_run(&R, runs + run);
     __syncthreads();
-    run_grid<FitT, QPL>(R, local, smem, status, &s_flag);
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) unsigned long long tc_mbar;
+    TcState tcs{0u, 0u, 0u};
+    if (R.plan.tc) tc_setup(tcs, &tmem_slot, &tc_mbar);
+    run_grid<FitT, QPL>(R, local, smem, status, &s_flag, tcs);
+    if (R.plan.tc) tc_teardown(tcs);
 }
 
 // ------------------------------------------------------- evaluation hook

@@ -28,6 +28,7 @@ struct Smem {
     int* otsu;
     void* red;
     uint8_t* nloc;
+    unsigned char *TA, *TY;   // tcgen05 rotation operands (plan.tc)
 };
 
 template <typename FitT>
@@ -58,6 +59,8 @@ __device__ __forceinline__ Smem<FitT> carve(unsigned char* base, const SmemPlan&
     S.P1 = reinterpret_cast<long long*>(base + L.P1);
     S.otsu = reinterpret_cast<int*>(base + L.otsu);
     S.red = base + L.red;
+    S.TA = base + L.TA;
+    S.TY = base + L.TY;
     return S;
 }
 
@@ -84,6 +87,15 @@ __device__ __forceinline__ void load_constants(const ApoRun& R, const Smem<FitT>
         for (int i = threadIdx.x; i < n4; i += blockDim.x) {
             dst[i] = sh[i];
             dst[n4 + i] = sl[i];
+        }
+    }
+    if (R.plan.tc) {
+        // canonical-layout rotation parts: Th then Tl, Np * Np halves each
+        const int n16 = P.Np * P.Np / 8;
+        uint4* dst = reinterpret_cast<uint4*>(S.TA);
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) {
+            dst[i] = C.Th[i];
+            dst[n16 + i] = C.Tl[i];
         }
     }
     if (P.kind == kOtsu) {

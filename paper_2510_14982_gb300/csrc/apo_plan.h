@@ -20,8 +20,15 @@ inline int plan_pow2(int v)
 // Layout for a run of population ps (0 for the evaluation hooks).  grid
 // selects the cooperative-grid layout (512 threads, 64-row chunks);
 // otherwise the resident / work-queue layout (256 threads, 32-row chunks).
+// tc (grid only) places the tcgen05 rotation operands: TA, the rotation's
+// fp16 hi and lo parts (Np x Np each, canonical UMMA layout), then directly
+// after it TY, the chunk's split candidates (kTcN x Np each).  The MMAs read
+// kTcM rotation rows; rows Np..kTcM-1 of the lo part fall into TY (never
+// beyond it, since (kTcM - Np) Np 2 <= 4 kTcN Np) and only produce
+// accumulator rows that are not read.
+static_assert(kGridChunk == kTcN, "the tcgen05 rotation takes a whole grid chunk per MMA");
 inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool mt_smem, bool grid,
-                               int chunk = 0)
+                               int chunk = 0, bool tc = false)
 {
     const bool fit64 = P->kind == 6;
     const size_t fsz = fit64 ? 8 : 4;
@@ -53,6 +60,9 @@ inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool
     L.perm1 = take((size_t)L.ps_pad * 4);
     L.keys = take((size_t)L.ps_pad * (fit64 ? 16 : 8));
     L.MT = take(mt_smem ? (size_t)2 * Np * P->dev.bws * 4 : 0);
+    L.tc = tc;
+    L.TA = take(tc ? (size_t)4 * Np * Np : 0);
+    L.TY = take(tc ? (size_t)4 * kTcN * Np : 0);
     L.o = take(Dp * 4);
     L.lb = take(Dp * 4);
     L.ub = take(Dp * 4);
@@ -78,6 +88,11 @@ inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool
 inline SmemPlan choose_plan(const apo_problem* P, int ps, bool resident, bool grid, size_t smem_max)
 {
     const bool can = P->ncomp == 1 && P->dev.comp[0].MT;
+    if (grid && can && P->dev.comp[0].Th) {
+        // the grid kernel's rotation on tcgen05
+        SmemPlan L = make_smem_plan(P, ps, resident, false, grid, kGridChunk, true);
+        if (L.total <= smem_max) return L;
+    }
     if (can) {
         SmemPlan L = make_smem_plan(P, ps, resident, true, grid);
         if (L.total <= smem_max) return L;
