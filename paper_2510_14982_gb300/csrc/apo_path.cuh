@@ -476,30 +476,26 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     }
     const int si = (int)(ei & kSlotMask), sa = (int)(ea & kSlotMask), sb = (int)(eb & kSlotMask);
     const float2 *pi = row_of(ei), *pj = row_of(ej), *pa = row_of(ea), *pb = row_of(eb);
+    // Every lane loads an in-bounds pair of all four rows unconditionally
+    // (rows the mode does not use alias X_i, lanes past D repeat the last
+    // pair), so no load sits behind a branch whose join would wait for it:
+    // the loads stay in flight through the draws and the mask selection
+    // below.  Values the mode or the lane does not use are never read.
+    const int qmax = ((D + 1) >> 1) - 1;
     float xi[2 * QPL], xj[2 * QPL], xa[2 * QPL], xb[2 * QPL];
 #pragma unroll
     for (int j = 0; j < QPL; ++j) {
-        const int q = lane + 32 * j;
-        float2 vi = make_float2(0.f, 0.f), vj = vi, va = vi, vb = vi;
-        if (2 * q < D) {
-            vi = ldst(pi + q, res);
-            if (mode == kAutotrophic) vj = ldst(pj + q, res);
-            if (forage) {
-                va = ldst(pa + q, res);
-                vb = ldst(pb + q, res);
-            }
-        }
+        const int q = min(lane + 32 * j, qmax);
+        const float2 vi = ldst(pi + q, res), vj = ldst(pj + q, res);
+        const float2 va = ldst(pa + q, res), vb = ldst(pb + q, res);
         xi[2 * j] = vi.x; xi[2 * j + 1] = vi.y;
         xj[2 * j] = vj.x; xj[2 * j + 1] = vj.y;
         xa[2 * j] = va.x; xa[2 * j + 1] = va.y;
         xb[2 * j] = vb.x; xb[2 * j + 1] = vb.y;
     }
-    float fa = 0.f, fb = 1.f;
-    if (forage) {
-        fa = (float)ldst(F + sa, res);
-        fb = (float)ldst(F + sb, res);
-    }
-    if (lane == 0) S.rowF[R.plan.chunk + row] = ldst(F + si, res);   // old fitness for the greedy step
+    const float fa = (float)ldst(F + sa, res), fb = (float)ldst(F + sb, res);
+    // old fitness for the greedy step, stored at the end of the row
+    const FitT fold = ldst(F + si, res);
 
     // per-dimension draws and the mask (independent of the gathered rows,
     // overlapping their latency)
@@ -614,6 +610,7 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
                 xo[q] = make_float2(2 * q < D ? xi[2 * j] : 0.f, 2 * q + 1 < D ? xi[2 * j + 1] : 0.f);
         }
     }
+    if (lane == 0) S.rowF[R.plan.chunk + row] = fold;
 }
 
 
