@@ -224,7 +224,8 @@ __device__ __forceinline__ void run_one(const ApoRun& R, int local, unsigned cha
         for (int c0 = r0; c0 < r1; c0 += CH) {
             const int rows = min(CH, r1 - c0);
             for (int row = warp; row < rows; row += nw)
-                gen_step_row<FitT, QPL>(R, S, Xs[cur], nullptr, Fs[cur], perm, res, true, t, c0 + row, row);
+                gen_step_row<FitT, QPL>(R, S, Xs[cur], nullptr, Fs[cur], perm, res, true, t, c0 + row,
+                                        dr_state(R, t, c0 + row), row);
             __syncthreads();
             eval_chunk<FitT>(R, S, rows);
             // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i).
@@ -440,6 +441,9 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
     const bool count_rank = nown <= 2 * NT && g >= 2;
     KT* skeys = count_rank ? keys + npad : keys;
     int* hist = reinterpret_cast<int*>(S.perm[1]);   // [nown]: other keys per own position
+    // [nown]: the own positions' dormancy inputs of the iteration, in the
+    // words of hist, which are free from barrier B to the next R2
+    uint32_t* drs = S.perm[1];
     for (int r = tid; r < ps; r += NT) perm[r] = (uint32_t)r;
     __syncthreads();
 
@@ -527,8 +531,12 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
         }
         if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
 
-        // R3: the new permutation; its head is the best of iteration t - 1
+        // R3: the new permutation; its head is the best of iteration t - 1.
+        // The own positions' dormancy inputs are fetched alongside, all at
+        // once, so that no row's mode waits on a global load.
         copy_cg(perm, R.perm_g, ps);
+        if (t <= R.t_end)
+            for (int m = tid; m < nown; m += NT) drs[m] = dr_state(R, t, pos_of(m));
         __syncthreads();
         if (local == 0) {
             const uint32_t eb = perm[0];
@@ -548,7 +556,8 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
         for (int c0 = 0; c0 < nown; c0 += CH) {
             const int rows = min(CH, nown - c0);
             for (int row = warp; row < rows; row += nw)
-                gen_step_row<FitT, QPL>(R, S, Xs[0], Xs[1], Fs[cur], perm, false, false, t, pos_of(c0 + row), row);
+                gen_step_row<FitT, QPL>(R, S, Xs[0], Xs[1], Fs[cur], perm, false, false, t, pos_of(c0 + row),
+                                        drs[c0 + row], row);
             __syncthreads();
             if (!evaluate(rows)) return;
             // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i).

@@ -385,6 +385,18 @@ __device__ __forceinline__ T ldst(const T* p, bool resident)
 }
 
 // ------------------------------------------------- candidate generation
+// Dormancy/reproduction input of rank position r at iteration t: bit 31 set
+// when r is in Dr_index (Algorithm 1); the low bits hold its p_dr threshold
+// ceil(p_dr 2^24) (Eq. 4, below 2^25).  Both loads are unconditional, so
+// neither waits behind the other.
+__device__ __forceinline__ uint32_t dr_state(const ApoRun& R, int t, int r)
+{
+    const int W = (R.ps + 31) >> 5;
+    const uint32_t word = R.drmask[(size_t)t * W + (r >> 5)];
+    const uint32_t thr = R.thr_dr[r];
+    return ((word >> (r & 31)) & 1u) ? (0x80000000u | thr) : 0u;
+}
+
 // Population initialisation (Algorithm 1): X_p = Xmin + U (Xmax - Xmin).
 template <typename FitT, int QPL>
 __device__ __forceinline__ void gen_init_row(const ApoRun& R, const Smem<FitT>& S, int p, int row)
@@ -422,7 +434,7 @@ __device__ __forceinline__ void gen_init_row(const ApoRun& R, const Smem<FitT>& 
 template <typename FitT, int QPL>
 __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* __restrict__ X,
                              const float* __restrict__ X1, const FitT* __restrict__ F, const uint32_t* perm,
-                             bool res, bool keep_old, int t, int r, int row, int cand = 0)
+                             bool res, bool keep_old, int t, int r, uint32_t drs, int row, int cand = 0)
 {
     // candidate c of the surrogate-assisted form draws from slots | (c << 8);
     // c = 0 is the plain candidate
@@ -450,11 +462,10 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     sc.x = __shfl_sync(0xffffffffu, jw.x, jb); sc.y = __shfl_sync(0xffffffffu, jw.y, jb);
     sc.z = __shfl_sync(0xffffffffu, jw.z, jb); sc.w = __shfl_sync(0xffffffffu, jw.w, jb);
     sc2.x = __shfl_sync(0xffffffffu, jw.x, jb + 1); sc2.y = __shfl_sync(0xffffffffu, jw.y, jb + 1);
-    const int W = (ps + 31) >> 5;
-    const bool in_dr = (R.drmask[(size_t)t * W + (r >> 5)] >> (r & 31)) & 1u;
+    const bool in_dr = (drs >> 31) != 0u;
     const uint32_t mm = m24p1(sc.x);
     int mode;
-    if (in_dr) mode = (mm < R.thr_dr[r]) ? kDormancy : kReproduction;
+    if (in_dr) mode = (mm < (drs & 0x7FFFFFFFu)) ? kDormancy : kReproduction;
     else mode = (mm < R.thr_ah[t]) ? kAutotrophic : kHeterotrophic;
     const bool forage = mode == kAutotrophic || mode == kHeterotrophic;
 
@@ -463,17 +474,17 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
         const float* base = (X1 != nullptr && (e & kLocBit)) ? X1 : X;
         return reinterpret_cast<const float2*>(base + (size_t)(e & kSlotMask) * Dp);
     };
+    // the candidate rows of both foraging modes are looked up together and
+    // selected by the mode (no branch to wait at)
     const uint32_t ei = perm[r];
-    uint32_t ej = ei, ea = ei, eb = ei;
-    if (mode == kAutotrophic) {
-        ej = perm[idx_draw(sc2.y, (uint32_t)ps)];
-        const uint32_t p0 = __shfl_sync(0xffffffffu, jw.x, jb + 2), p1 = __shfl_sync(0xffffffffu, jw.y, jb + 2);
-        ea = perm[idx_draw(p0, (uint32_t)ps)];
-        eb = perm[idx_draw(p1, (uint32_t)ps)];
-    } else if (mode == kHeterotrophic) {
-        ea = perm[r - 1 < 0 ? 0 : r - 1];
-        eb = perm[r + 1 > ps - 1 ? ps - 1 : r + 1];
-    }
+    const uint32_t p0 = __shfl_sync(0xffffffffu, jw.x, jb + 2), p1 = __shfl_sync(0xffffffffu, jw.y, jb + 2);
+    const uint32_t aj = perm[idx_draw(sc2.y, (uint32_t)ps)];
+    const uint32_t aa = perm[idx_draw(p0, (uint32_t)ps)], ab = perm[idx_draw(p1, (uint32_t)ps)];
+    const uint32_t ha = perm[r - 1 < 0 ? 0 : r - 1], hb = perm[r + 1 > ps - 1 ? ps - 1 : r + 1];
+    const bool autot = mode == kAutotrophic, het = mode == kHeterotrophic;
+    const uint32_t ej = autot ? aj : ei;
+    uint32_t ea = autot ? aa : (het ? ha : ei);   // reassigned per pair when np > 1
+    uint32_t eb = autot ? ab : (het ? hb : ei);
     const int si = (int)(ei & kSlotMask), sa = (int)(ea & kSlotMask), sb = (int)(eb & kSlotMask);
     const float2 *pi = row_of(ei), *pj = row_of(ej), *pa = row_of(ea), *pb = row_of(eb);
     // Every lane loads an in-bounds pair of all four rows unconditionally
