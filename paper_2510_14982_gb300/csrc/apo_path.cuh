@@ -442,6 +442,11 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     const int lane = threadIdx.x & 31;
     const int D = R.prob.D, Dp = R.prob.Dp, ps = R.ps, np = R.np;
     const uint32_t seed = R.seed, run = R.run;
+    // the iteration's scalars (Eq. 7, Eq. 9, Eq. 11) are requested first, so
+    // that their latency overlaps the draws
+    const uint32_t thr_ah = R.thr_ah[t];
+    const float fsc = R.fsc[t], nsc = R.nsc[t];
+    const float inv_np = 1.f / (float)np;
     // Per-protozoon draws, from lanes jb + u: u = 0 SCAL, u = 1 SCAL2,
     // u = 2 + k PAIR k.  The last per-dimension call of a lane covers pairs
     // q = lane + 32 (QPL - 1), of which only q < ceil(D / 2) exist; when at
@@ -466,7 +471,7 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     const uint32_t mm = m24p1(sc.x);
     int mode;
     if (in_dr) mode = (mm < (drs & 0x7FFFFFFFu)) ? kDormancy : kReproduction;
-    else mode = (mm < R.thr_ah[t]) ? kAutotrophic : kHeterotrophic;
+    else mode = (mm < thr_ah) ? kAutotrophic : kHeterotrophic;
     const bool forage = mode == kAutotrophic || mode == kHeterotrophic;
 
     // rows from the snapshot: X_i, X_j (autotrophic) and the first pair
@@ -576,11 +581,9 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
 #pragma unroll
         for (int e = 0; e < 2 * QPL; ++e) acc[e] = 0.f;
     }
-    const float inv_np = 1.f / (float)np;
-    const float ff = forage ? u01(sc.y) * R.fsc[t] : 0.f;
+    const float ff = forage ? u01(sc.y) * fsc : 0.f;
     const float s = sign_draw(sc.z);
     const float rho = u01(sc.w);
-    const float nsc = R.nsc[t];
 
     float2* xc = reinterpret_cast<float2*>(S.Xc + (size_t)row * Dp);
     float2* xo = reinterpret_cast<float2*>(S.Xo + (size_t)row * Dp);
