@@ -6,6 +6,8 @@
 
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "apo_device.cuh"
 
 namespace apo {
@@ -587,42 +589,52 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
 
     float2* xc = reinterpret_cast<float2*>(S.Xc + (size_t)row * Dp);
     float2* xo = reinterpret_cast<float2*>(S.Xo + (size_t)row * Dp);
+    // The candidate, one loop per mode (uniform over the warp): the mask bit
+    // of a lane is a select, and lanes past D read the bounds of dimension
+    // D - 1 and write zeros, so the loop body has no divergent branch.
+    auto emit = [&](auto mode_c) {
+        constexpr int M = decltype(mode_c)::value;
 #pragma unroll
-    for (int j = 0; j < QPL; ++j) {
-        const int q = lane + 32 * j;
-        float out[2];
+        for (int j = 0; j < QPL; ++j) {
+            const int q = lane + 32 * j;
+            float out[2];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int d = 2 * q + e;
-            const int sl = 2 * j + e;
-            out[e] = 0.f;
-            if (d < D) {
-                const float lb = S.lb[d], ub = S.ub[d];
-                const bool mk = (mask >> sl) & 1u;
+            for (int e = 0; e < 2; ++e) {
+                const int d = 2 * q + e;
+                const int sl = 2 * j + e;
+                const int dc = d < D ? d : D - 1;
+                const float lb = S.lb[dc], ub = S.ub[dc];
                 const float x0 = xi[sl];
-                float x = x0;
-                if (mode == kDormancy) {
+                float x;
+                if constexpr (M == kDormancy) {
                     x = fmaf(u01(A[sl]), ub - lb, lb);                          // Eq. 1
-                } else if (mk) {
-                    if (mode == kReproduction) {
+                } else {
+                    if constexpr (M == kReproduction) {
                         x = x0 + s * rho * fmaf(u01(A[sl]), ub - lb, lb);       // Eq. 2
-                    } else if (mode == kAutotrophic) {
+                    } else if constexpr (M == kAutotrophic) {
                         x = x0 + ff * (xj[sl] - x0 + acc[sl] * inv_np);         // Eq. 6
                     } else {
                         const float xnear = (1.f + s * u01(A[sl]) * nsc) * x0;  // Eq. 9
                         x = x0 + ff * (xnear - x0 + acc[sl] * inv_np);          // Eq. 8
                     }
+                    x = ((mask >> sl) & 1u) ? x : x0;                           // Eq. 3, 5
                 }
-                out[e] = fminf(fmaxf(x, lb), ub);
+                out[e] = d < D ? fminf(fmaxf(x, lb), ub) : 0.f;
+            }
+            // Dp is a multiple of 4, so a pair starting below Dp lies inside
+            // the row; the padding past D is written as zeros
+            if (2 * q < Dp) {
+                xc[q] = make_float2(out[0], out[1]);
+                if (keep_old)
+                    xo[q] = make_float2(2 * q < D ? xi[2 * j] : 0.f, 2 * q + 1 < D ? xi[2 * j + 1] : 0.f);
             }
         }
-        // Dp is a multiple of 4, so a pair starting below Dp lies inside the
-        // row; the padding past D is written as zeros
-        if (2 * q < Dp) {
-            xc[q] = make_float2(out[0], out[1]);
-            if (keep_old)
-                xo[q] = make_float2(2 * q < D ? xi[2 * j] : 0.f, 2 * q + 1 < D ? xi[2 * j + 1] : 0.f);
-        }
+    };
+    switch (mode) {
+    case kDormancy: emit(std::integral_constant<int, kDormancy>{}); break;
+    case kReproduction: emit(std::integral_constant<int, kReproduction>{}); break;
+    case kAutotrophic: emit(std::integral_constant<int, kAutotrophic>{}); break;
+    default: emit(std::integral_constant<int, kHeterotrophic>{}); break;
     }
     if (lane == 0) S.rowF[R.plan.chunk + row] = fold;
 }
