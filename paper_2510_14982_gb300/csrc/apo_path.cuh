@@ -249,6 +249,71 @@ __device__ __forceinline__ float seg_value(const float* z, int zs, const DevComp
     return warp_sum(s);
 }
 
+// seg_value of NR rows at once (elements contiguous): the same per-lane
+// accumulation order and warp sum per row as seg_value, with the rows'
+// element work and reductions interleaved.
+template <int NR>
+__device__ __forceinline__ void seg_values(const float* const (&z)[NR], const DevComp& C, const float* ew, int D,
+                                           float (&out)[NR])
+{
+    const int lane = threadIdx.x & 31;
+    float s[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) s[i] = 0.f;
+    for (int d = lane; d < D; d += 32) {
+        if (d < C.s1) {
+            const float w = ew[d];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const float v = z[i][d];
+                s[i] = fmaf(w * v, v, s[i]);
+            }
+        } else if (d < C.s2) {
+            if (d + 1 < C.s2) {
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    const float v = z[i][d];
+                    const float a = z[i][d + 1] - v * v;
+                    const float b = v - 1.f;
+                    s[i] += 100.f * a * a + b * b;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const float v = z[i][d];
+                s[i] += v * v - 10.f * cospif(2.f * v) + 10.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int i = 0; i < NR; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], off);
+#pragma unroll
+    for (int i = 0; i < NR; ++i) out[i] = s[i];
+}
+
+// Objective of the rows [0, rows) of the Z tile (rows Np apart) into rowF:
+// warp w takes rows w, w + nw, w + 2 nw, w + 3 nw together.
+template <typename FitT>
+__device__ __forceinline__ void zrows_to_f(const Smem<FitT>& S, const DevComp& C, int D, int Np, int rows)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r0 = warp; r0 < rows; r0 += 4 * nw) {
+        // rows past the last one repeat it (computed, not stored)
+        const float* z[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) z[i] = S.Zc + (size_t)min(r0 + i * nw, rows - 1) * Np;
+        float f[4];
+        seg_values<4>(z, C, S.ew, D, f);
+        if (lane == 0)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (r0 + i * nw < rows) S.rowF[r0 + i * nw] = (FitT)f[i];
+    }
+}
+
 // Otsu between-class variance of one row by one warp (thresholds in lanes
 // 0..T-1), negated.  The thresholds are sorted by rank counting; lane c then
 // fetches the precomputed float64 term of class c (the bin range between
@@ -320,10 +385,7 @@ __device__ __forceinline__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S,
             tile_gemm_f16x3<false>(S.Xc, Dp, S.o, C.Bh, C.Bl, P.bws, C.ysc, C.zsc, S.Zc, Np, rows, D);
         }
         __syncthreads();
-        for (int row = warp; row < rows; row += nw) {
-            const float v = seg_value(S.Zc + (size_t)row * Np, 1, P.comp[0], S.ew, D);
-            if (lane == 0) S.rowF[row] = (FitT)v;
-        }
+        zrows_to_f<FitT>(S, P.comp[0], D, Np, rows);
         __syncthreads();
         return;
     }

@@ -185,10 +185,7 @@ __device__ bool eval_chunk_tc(const ApoRun& R, const Smem<FitT>& S, int rows, Tc
     // the next chunk's MMAs overwrite the accumulator only after every read
     asm volatile("tcgen05.fence::before_thread_sync;" : : : "memory");
     __syncthreads();
-    for (int row = warp; row < rows; row += nw) {
-        const float f = seg_value(S.Zc + (size_t)row * Np, 1, C, S.ew, D);
-        if (lane == 0) S.rowF[row] = (FitT)f;
-    }
+    zrows_to_f<FitT>(S, C, D, Np, rows);
     __syncthreads();
     return true;
 }
