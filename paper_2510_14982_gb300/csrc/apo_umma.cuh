@@ -116,7 +116,11 @@ __device__ bool eval_chunk_tc(const ApoRun& R, const Smem<FitT>& S, int rows, Tc
     // TY: y = ysc (x - o) of the chunk rows as fp16 hi and lo parts, zero for
     // rows >= rows and k >= D.  Task i covers 8 k of one row; 8 consecutive
     // tasks are the 8 rows of one core matrix, so a quarter-warp's 16-byte
-    // stores fill 128 contiguous bytes.
+    // stores fill 128 contiguous bytes, and (rows Dp floats apart, Dp a
+    // multiple of 4) its 16-byte loads of x fall on distinct banks when Dp is
+    // 4 mod 8.  The last 16-byte group of a row may read past Dp (into the
+    // next row, or the region after the candidates, or past o): those k are
+    // >= D and masked.
     const int nkb = Np >> 3;
     const float ysc = C.ysc;
     unsigned char* yh = S.TY;
@@ -124,13 +128,17 @@ __device__ bool eval_chunk_tc(const ApoRun& R, const Smem<FitT>& S, int rows, Tc
     for (int i = tid; i < kTcN * nkb; i += blockDim.x) {
         const int r = (i & 7) + 8 * (i / (8 * nkb));
         const int kb = (i >> 3) % nkb;
-        const float* xr = S.Xc + (size_t)r * Dp;
+        const float4* xr = reinterpret_cast<const float4*>(S.Xc + (size_t)r * Dp + 8 * kb);
+        const float4* orow = reinterpret_cast<const float4*>(S.o + 8 * kb);
+        const float4 x0 = xr[0], x1 = xr[1], o0 = orow[0], o1 = orow[1];
+        const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        const float ov[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
         uint32_t h[4], l[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int k = 8 * kb + 2 * e;
-            const float y0 = (r < rows && k < D) ? (xr[k] - S.o[k]) * ysc : 0.f;
-            const float y1 = (r < rows && k + 1 < D) ? (xr[k + 1] - S.o[k + 1]) * ysc : 0.f;
+            const float y0 = (r < rows && k < D) ? (xv[2 * e] - ov[2 * e]) * ysc : 0.f;
+            const float y1 = (r < rows && k + 1 < D) ? (xv[2 * e + 1] - ov[2 * e + 1]) * ysc : 0.f;
             split_f16x2(y0, y1, h[e], l[e]);
         }
         const uint32_t off = umma_off(r, 8 * kb, Np);
@@ -145,13 +153,17 @@ __device__ bool eval_chunk_tc(const ApoRun& R, const Smem<FitT>& S, int rows, Tc
         asm volatile("tcgen05.fence::after_thread_sync;" : : : "memory");
         const uint32_t ah = (uint32_t)__cvta_generic_to_shared(S.TA);
         const uint32_t al = ah + (uint32_t)(Np * Np * 2);
-        const uint32_t bh = (uint32_t)__cvta_generic_to_shared(yh);
-        const uint32_t bl = (uint32_t)__cvta_generic_to_shared(yl);
+        // a K step advances every operand by two core matrices (256 bytes),
+        // i.e. 16 in the descriptor's address field (which cannot carry:
+        // shared addresses stay below 2^18)
+        uint64_t dah = umma_kdesc(ah, Np), dal = umma_kdesc(al, Np);
+        uint64_t dbh = umma_kdesc((uint32_t)__cvta_generic_to_shared(yh), Np);
+        uint64_t dbl = umma_kdesc((uint32_t)__cvta_generic_to_shared(yl), Np);
         for (int s = 0; s < (Np >> 4); ++s) {
-            const uint32_t ko = 256u * (uint32_t)s;   // two core matrices of K per step
-            umma_f16(st.tmem, umma_kdesc(ah + ko, Np), umma_kdesc(bl + ko, Np), s > 0 ? 1u : 0u);
-            umma_f16(st.tmem, umma_kdesc(al + ko, Np), umma_kdesc(bh + ko, Np), 1u);
-            umma_f16(st.tmem, umma_kdesc(ah + ko, Np), umma_kdesc(bh + ko, Np), 1u);
+            umma_f16(st.tmem, dah, dbl, s > 0 ? 1u : 0u);
+            umma_f16(st.tmem, dal, dbh, 1u);
+            umma_f16(st.tmem, dah, dbh, 1u);
+            dah += 16u; dal += 16u; dbh += 16u; dbl += 16u;
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :
