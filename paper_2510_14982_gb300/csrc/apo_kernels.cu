@@ -326,20 +326,30 @@ __device__ __forceinline__ ulonglong2 lds_key(uint32_t a, ulonglong2*)
     return v;
 }
 
-// Number of keys of the sorted shared-memory segment seg[0, len) below k.
-template <typename FitT>
-__device__ __forceinline__ int lower_bound_key(const typename KeyOf<FitT>::T* seg, int len,
-                                               typename KeyOf<FitT>::T k)
+// Numbers of keys of the sorted shared-memory segment seg[0, len) below each
+// of NK keys: a descent in power-of-two steps
+// (p += step while seg[p + step - 1] < k; p is then the number of keys below
+// k, since len < 2 P), with the same steps for every key, so that their
+// shared-memory loads overlap instead of running one search after another.
+template <typename FitT, int NK>
+__device__ __forceinline__ void lower_bound_keys(const typename KeyOf<FitT>::T* seg, int len,
+                                                 const typename KeyOf<FitT>::T (&k)[NK], int (&p)[NK])
 {
     using KT = typename KeyOf<FitT>::T;
     const uint32_t base = (uint32_t)__cvta_generic_to_shared(seg);
-    int lo = 0, hi = len;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (KeyOf<FitT>::less(lds_key(base + (uint32_t)(mid * sizeof(KT)), (KT*)nullptr), k)) lo = mid + 1;
-        else hi = mid;
+#pragma unroll
+    for (int u = 0; u < NK; ++u) p[u] = 0;
+    if (len <= 0) return;
+    int P = 1;
+    while (2 * P <= len) P <<= 1;
+    for (int step = P; step > 0; step >>= 1) {
+#pragma unroll
+        for (int u = 0; u < NK; ++u) {
+            const int q = p[u] + step;
+            const KT v = lds_key(base + (uint32_t)((min(q, len) - 1) * (int)sizeof(KT)), (KT*)nullptr);
+            if (q <= len && KeyOf<FitT>::less(v, k[u])) p[u] = q;
+        }
     }
-    return lo;
 }
 
 // Copies n elements from global (L2, bypassing L1) to shared memory with
@@ -511,17 +521,16 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
             KT y[8];
             bool ok[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {   // eight loads in flight
+            for (int u = 0; u < 8; ++u) {   // eight loads in flight, none behind a branch
                 const int j = j0 + u * NT;
                 ok[u] = j < ps && (j < kb || j >= kb + nown);
-                if (ok[u]) y[u] = __ldcg(keys_g + j);
+                y[u] = __ldcg(keys_g + min(j, ps - 1));
             }
+            int p[8];
+            lower_bound_keys<FitT, 8>(skeys, nown, y, p);   // the eight searches in lockstep
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                if (ok[u]) {
-                    const int p = lower_bound_key<FitT>(skeys, nown, y[u]);
-                    if (p < nown) atomicAdd(&hist[p], 1);
-                }
+                if (ok[u] && p[u] < nown) atomicAdd(&hist[p[u]], 1);
         }
         __syncthreads();
         block_scan_inclusive(hist, nown, reinterpret_cast<int*>(S.red));
