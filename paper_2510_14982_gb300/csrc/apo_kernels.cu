@@ -547,10 +547,14 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
         if (t <= R.t_end)
             for (int m = tid; m < nown; m += NT) drs[m] = dr_state(R, t, pos_of(m));
         __syncthreads();
+        // the curve value is loaded here and stored after the greedy step, so
+        // that no warp waits for the load
+        FitT curve_v = (FitT)0;
+        const bool curve_w = local == 0 && tid == 0 && R.curve != nullptr;
         if (local == 0) {
             const uint32_t eb = perm[0];
             const int bslot = (int)(eb & kSlotMask);
-            if (tid == 0 && R.curve) R.curve[t - 1] = (float)ldst(Fs[cur] + bslot, false);
+            if (curve_w) curve_v = ldst(Fs[cur] + bslot, false);
             if (t > R.t_end) {
                 if (tid == 0 && R.best_f) *R.best_f = (double)ldst(Fs[cur] + bslot, false);
                 if (R.best_x) {
@@ -559,7 +563,10 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
                 }
             }
         }
-        if (t > R.t_end) break;
+        if (t > R.t_end) {
+            if (curve_w) R.curve[t - 1] = (float)curve_v;
+            break;
+        }
 
         // the own positions: generate, evaluate, replace
         for (int c0 = 0; c0 < nown; c0 += CH) {
@@ -573,27 +580,33 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
             // An accepted row goes to the slot's other buffer (nobody reads it
             // in this iteration) and flips the slot's buffer bit; a rejected
             // one stays where it is.  The kept fitness also forms the own sort
-            // key of the next iteration.
-            for (int row = warp; row < rows; row += nw) {
+            // key of the next iteration.  One thread per row decides; the
+            // accepted rows are copied by the whole CTA, one 16-byte group
+            // per thread.
+            for (int row = tid; row < rows; row += NT) {
                 const uint32_t e = perm[pos_of(c0 + row)];
                 const int slot = (int)(e & kSlotMask);
                 const uint32_t loc = e >> 31;
                 const FitT fo = S.rowF[CH + row];
                 const FitT fn = S.rowF[row];
                 const bool acc = fn < fo;
-                if (acc) {
+                Fs[cur ^ 1][slot] = acc ? fn : fo;
+                keys[c0 + row] = KO::make(acc ? fn : fo, (uint32_t)pos_of(c0 + row));
+                nloc[c0 + row] = (uint8_t)(acc ? (loc ^ 1u) : loc);
+            }
+            const int g4 = Dp >> 2;
+            for (int i = tid; i < rows * g4; i += NT) {
+                const int row = i / g4, v = i - row * g4;
+                if (S.rowF[row] < S.rowF[CH + row]) {
+                    const uint32_t e = perm[pos_of(c0 + row)];
                     const float4* src = reinterpret_cast<const float4*>(S.Xc + (size_t)row * Dp);
-                    float4* dst = reinterpret_cast<float4*>(Xs[loc ^ 1u] + (size_t)slot * Dp);
-                    for (int v = lane; v < (Dp >> 2); v += 32) dst[v] = src[v];
-                }
-                if (lane == 0) {
-                    Fs[cur ^ 1][slot] = acc ? fn : fo;
-                    keys[c0 + row] = KO::make(acc ? fn : fo, (uint32_t)pos_of(c0 + row));
-                    nloc[c0 + row] = (uint8_t)(acc ? (loc ^ 1u) : loc);
+                    float4* dst = reinterpret_cast<float4*>(Xs[(e >> 31) ^ 1u] + (size_t)(e & kSlotMask) * Dp);
+                    dst[v] = src[v];
                 }
             }
             __syncthreads();
         }
+        if (curve_w) R.curve[t - 1] = (float)curve_v;
         keys_ready = true;
         cur ^= 1;
         if (step_out && t == R.t_end) {
