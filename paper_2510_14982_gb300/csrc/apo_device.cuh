@@ -382,24 +382,32 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
 }
 
-// Barrier over the g CTAs of one run.  bar[0] counts arrivals and is never
-// reset: the CTA's n-th barrier (n = ++gen) is passed once the count reaches
-// n g.  After the CTA-wide __syncthreads, thread 0 arrives with one release
-// reduction (cumulative over the CTA's writes) and polls with acquire loads,
-// so a barrier costs one trip to L2 plus the polling delay.  bar[2] is the
-// run's abort flag: every 64 polls the waiter checks it and the 4 s limit; a
-// wait that runs out sets APO_ERR_TIMEOUT and the flag.  Returns false (for
-// every thread of the CTA) when the run was aborted or the wait timed out;
-// the caller then stops the run.
-__device__ __noinline__ static bool run_barrier(unsigned* bar, int g, unsigned& gen, int* status, int* s_flag)
+// Barrier over the g CTAs of one run, in two halves.  bar[0] counts arrivals
+// and is never reset: the CTA's n-th barrier (n = ++gen) is passed once the
+// count reaches n g.  Arrival: after the CTA-wide __syncthreads, thread 0
+// arrives with one release reduction (cumulative over the CTA's writes so
+// far).  Wait: thread 0 polls with acquire loads, so a barrier costs one trip
+// to L2 plus the polling delay; writes a CTA issues between the halves are
+// not part of this barrier's release (a later barrier's arrival covers
+// them).  bar[2] is the run's abort flag: every 64 polls the waiter checks
+// it and the 4 s limit; a wait that runs out sets APO_ERR_TIMEOUT and the
+// flag.  The wait returns false (for every thread of the CTA) when the run
+// was aborted or the wait timed out; the caller then stops the run.
+__device__ __forceinline__ void run_barrier_arrive(unsigned* bar, int g, unsigned& gen)
 {
     __syncthreads();
+    if (g > 1 && threadIdx.x == 0) {
+        ++gen;
+        red_release_add(&bar[0], 1u);
+    }
+}
+
+__device__ __noinline__ static bool run_barrier_wait(unsigned* bar, int g, unsigned gen, int* status, int* s_flag)
+{
     if (g > 1) {
         if (threadIdx.x == 0) {
             int ok = 1;
-            ++gen;
             const unsigned target = gen * (unsigned)g;
-            red_release_add(&bar[0], 1u);
             unsigned long long t0 = 0ull;
             for (unsigned n = 1;; ++n) {
                 if ((int)(ld_acquire(&bar[0]) - target) >= 0) break;
@@ -421,7 +429,14 @@ __device__ __noinline__ static bool run_barrier(unsigned* bar, int g, unsigned& 
         __syncthreads();
         return *s_flag != 0;
     }
+    __syncthreads();
     return true;
+}
+
+__device__ __forceinline__ bool run_barrier(unsigned* bar, int g, unsigned& gen, int* status, int* s_flag)
+{
+    run_barrier_arrive(bar, g, gen);
+    return run_barrier_wait(bar, g, gen, status, s_flag);
 }
 
 }  // namespace apo

@@ -473,6 +473,27 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
         }
     }
 
+    // Greedy writes of the chunk at c0 (rows rows, fitness and rows in Xc):
+    // the kept fitness of each row to Fd, and the accepted rows to their
+    // slots' other buffers, one 16-byte group per thread.
+    auto write_chunk = [&](int c0, int rows, FitT* Fd) {
+        for (int row = tid; row < rows; row += NT) {
+            const FitT fo = S.rowF[CH + row], fn = S.rowF[row];
+            Fd[perm[pos_of(c0 + row)] & kSlotMask] = fn < fo ? fn : fo;
+        }
+        const int g4 = Dp >> 2;
+        for (int i = tid; i < rows * g4; i += NT) {
+            const int row = i / g4, v = i - row * g4;
+            if (S.rowF[row] < S.rowF[CH + row]) {
+                const uint32_t e = perm[pos_of(c0 + row)];
+                const float4* src = reinterpret_cast<const float4*>(S.Xc + (size_t)row * Dp);
+                float4* dst = reinterpret_cast<float4*>(Xs[(e >> 31) ^ 1u] + (size_t)(e & kSlotMask) * Dp);
+                dst[v] = src[v];
+            }
+        }
+    };
+    int held_c0 = 0, held_rows = 0;   // greedy writes held for barrier A
+    FitT* held_F = nullptr;
     int cur = 0;
     bool keys_ready = false;   // the greedy step already wrote the own keys
     const bool step_out = (R.flags & kFlagStepOut) != 0;
@@ -510,7 +531,12 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
             bitonic_sort<KO>(keys, npad);
             for (int i = tid; i < nown; i += NT) keys_g[kb + i] = keys[i];
         }
-        if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
+        run_barrier_arrive(R.bar, g, bgen);
+        if (held_rows > 0) {
+            write_chunk(held_c0, held_rows, held_F);
+            held_rows = 0;
+        }
+        if (!run_barrier_wait(R.bar, g, bgen, status, s_flag)) return;
 
         // R2: distributed ranking.  An other key y lies above exactly the
         // p = lower_bound(own sorted keys, y) smallest own keys, so own key i
@@ -583,26 +609,26 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
             // key of the next iteration.  One thread per row decides; the
             // accepted rows are copied by the whole CTA, one 16-byte group
             // per thread.
+            // The last chunk's fitness and row writes are held until barrier
+            // A's arrival (below), so that its release need not wait for them
+            // to drain; nothing reads them before barrier B.  The step output
+            // reads them in this iteration, so it takes them here.
+            const bool hold = c0 + CH >= nown && !(step_out && t == R.t_end);
             for (int row = tid; row < rows; row += NT) {
                 const uint32_t e = perm[pos_of(c0 + row)];
-                const int slot = (int)(e & kSlotMask);
                 const uint32_t loc = e >> 31;
                 const FitT fo = S.rowF[CH + row];
                 const FitT fn = S.rowF[row];
                 const bool acc = fn < fo;
-                Fs[cur ^ 1][slot] = acc ? fn : fo;
                 keys[c0 + row] = KO::make(acc ? fn : fo, (uint32_t)pos_of(c0 + row));
                 nloc[c0 + row] = (uint8_t)(acc ? (loc ^ 1u) : loc);
             }
-            const int g4 = Dp >> 2;
-            for (int i = tid; i < rows * g4; i += NT) {
-                const int row = i / g4, v = i - row * g4;
-                if (S.rowF[row] < S.rowF[CH + row]) {
-                    const uint32_t e = perm[pos_of(c0 + row)];
-                    const float4* src = reinterpret_cast<const float4*>(S.Xc + (size_t)row * Dp);
-                    float4* dst = reinterpret_cast<float4*>(Xs[(e >> 31) ^ 1u] + (size_t)(e & kSlotMask) * Dp);
-                    dst[v] = src[v];
-                }
+            if (hold) {
+                held_c0 = c0;
+                held_rows = rows;
+                held_F = Fs[cur ^ 1];
+            } else {
+                write_chunk(c0, rows, Fs[cur ^ 1]);
             }
             __syncthreads();
         }
