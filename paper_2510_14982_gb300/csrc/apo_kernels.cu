@@ -536,13 +536,12 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
             write_chunk(held_c0, held_rows, held_F);
             held_rows = 0;
         }
+        for (int i = tid; i < nown; i += NT) hist[i] = 0;   // R2's counts (the wait ends synchronised)
         if (!run_barrier_wait(R.bar, g, bgen, status, s_flag)) return;
 
         // R2: distributed ranking.  An other key y lies above exactly the
         // p = lower_bound(own sorted keys, y) smallest own keys, so own key i
         // has sum_{p <= i} hist[p] other keys below it (keys are distinct).
-        for (int i = tid; i < nown; i += NT) hist[i] = 0;
-        __syncthreads();
         for (int j0 = tid; j0 < ps; j0 += 8 * NT) {
             KT y[8];
             bool ok[8];
@@ -564,14 +563,16 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
             const int pos = (int)KO::idx(skeys[i]);   // previous rank, an own position
             R.perm_g[i + hist[i]] = (perm[pos] & kSlotMask) | ((uint32_t)nloc[(pos - local) / g] << 31);
         }
-        if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
-
-        // R3: the new permutation; its head is the best of iteration t - 1.
-        // The own positions' dormancy inputs are fetched alongside, all at
-        // once, so that no row's mode waits on a global load.
-        copy_cg(perm, R.perm_g, ps);
+        // the own positions' dormancy inputs of iteration t are fetched
+        // while the barrier completes (all at once, so that no row's mode
+        // waits on a global load; hist is free after the arrival's sync)
+        run_barrier_arrive(R.bar, g, bgen);
         if (t <= R.t_end)
             for (int m = tid; m < nown; m += NT) drs[m] = dr_state(R, t, pos_of(m));
+        if (!run_barrier_wait(R.bar, g, bgen, status, s_flag)) return;
+
+        // R3: the new permutation; its head is the best of iteration t - 1.
+        copy_cg(perm, R.perm_g, ps);
         __syncthreads();
         // the curve value is loaded here and stored after the greedy step, so
         // that no warp waits for the load
