@@ -219,7 +219,10 @@ __device__ __forceinline__ void run_one(const ApoRun& R, int local, unsigned cha
         __syncthreads();
         pc ^= 1;
         perm = pnew;
-        if (local == 0 && tid == 0 && R.curve) R.curve[t - 1] = (float)ldst(Fs[cur] + perm[0], res);
+        // the curve value is stored after the greedy step, so that no warp
+        // waits for its load
+        const bool curve_w = local == 0 && tid == 0 && R.curve != nullptr;
+        const FitT curve_v = curve_w ? ldst(Fs[cur] + perm[0], res) : (FitT)0;
 
         for (int c0 = r0; c0 < r1; c0 += CH) {
             const int rows = min(CH, r1 - c0);
@@ -229,18 +232,24 @@ __device__ __forceinline__ void run_one(const ApoRun& R, int local, unsigned cha
             __syncthreads();
             eval_chunk<FitT>(R, S, rows);
             // Greedy replacement (Algorithm 1): keep X_new iff f(X_new) < f(X_i).
-            for (int row = warp; row < rows; row += nw) {
-                const int slot = (int)perm[c0 + row];
-                const FitT fo = S.rowF[CH + row];
-                const FitT fn = S.rowF[row];
-                const bool acc = fn < fo;
+            // Every row goes to the other buffer (the candidate if accepted,
+            // the old position otherwise): the kept fitness one thread per
+            // row, the rows one 16-byte group per thread.
+            for (int row = tid; row < rows; row += blockDim.x) {
+                const FitT fo = S.rowF[CH + row], fn = S.rowF[row];
+                Fs[cur ^ 1][perm[c0 + row]] = fn < fo ? fn : fo;
+            }
+            const int g4 = Dp >> 2;
+            for (int i = tid; i < rows * g4; i += blockDim.x) {
+                const int row = i / g4, v = i - row * g4;
+                const bool acc = S.rowF[row] < S.rowF[CH + row];
                 const float4* src = reinterpret_cast<const float4*>((acc ? S.Xc : S.Xo) + (size_t)row * Dp);
-                float4* dst = reinterpret_cast<float4*>(Xs[cur ^ 1] + (size_t)slot * Dp);
-                for (int v = lane; v < (Dp >> 2); v += 32) dst[v] = src[v];
-                if (lane == 0) Fs[cur ^ 1][slot] = acc ? fn : fo;
+                float4* dst = reinterpret_cast<float4*>(Xs[cur ^ 1] + (size_t)perm[c0 + row] * Dp);
+                dst[v] = src[v];
             }
             __syncthreads();
         }
+        if (curve_w) R.curve[t - 1] = (float)curve_v;
         if (!run_barrier(R.bar, g, bgen, status, s_flag)) return;
         cur ^= 1;
     }
