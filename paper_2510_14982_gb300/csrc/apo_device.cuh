@@ -319,9 +319,10 @@ static __constant__ RecipTable kRecip = make_recip_table();
 // smaller than every key at or above it, so index tie-breaks cannot arise).
 // The keys are uniform 32-bit Philox words, so interpolating between the
 // bracketing counts usually lands between the k-th and (k+1)-th smallest key
-// within a few warp-wide counts (about 3.2 on average for D in 10..200).  A
-// boundary tie, or no hit within ten counts (about 0.3% of selections),
-// falls back to the bitwise descent.  n = number of valid slots (<= 256).
+// within a few warp-wide counts (about 3.2 on average for D in 10..200 in
+// simulation; 3.5 measured in runs at D 100, ps 4096).  A boundary tie, or
+// no hit within ten counts (0.3 to 0.6% of selections), falls back to the
+// bitwise descent.  n = number of valid slots (<= 256).
 template <int QPL>
 __device__ uint32_t warp_kselect_interp(const uint32_t (&key)[2 * QPL], uint32_t valid, int k, int n)
 {

@@ -313,8 +313,9 @@ __global__ void __launch_bounds__(kThreads, 2) run_kernel(const ApoRun* __restri
 //   R2  the new rank of each own key = its position among the own keys plus
 //       the number of other segments' keys below it (the stable sort of
 //       Algorithm 1, distributed).  Every other key is located among the
-//       own sorted keys by binary search and counted there; a prefix sum
-//       of the counts gives the ranks; scatter perm_g[rank] = slot.  barrier B
+//       own sorted keys (eight keys per thread searched in lockstep) and
+//       counted there; a prefix sum of the counts gives the ranks; scatter
+//       perm_g[rank] = slot.                                      barrier B
 //   R3  copy perm_g (its head is the best of the population, the curve
 //       value), then generate, evaluate and replace the own positions.
 //       Each slot's current row lives in one of two buffers, named by the
@@ -322,6 +323,9 @@ __global__ void __launch_bounds__(kThreads, 2) run_kernel(const ApoRun* __restri
 //       other buffer, so the iteration's readers keep seeing the snapshot
 //       and rejected rows are never copied.  One more R1/R2 after the last
 //       iteration ranks the final population for the best.
+// Each grid barrier is an arrival and a wait; work no other CTA reads before
+// the next barrier (the last chunk's greedy writes, R2's zeroed counts, the
+// next iteration's dormancy inputs) goes between the two.
 __device__ __forceinline__ unsigned long long lds_key(uint32_t a, unsigned long long*)
 {
     unsigned long long v;
