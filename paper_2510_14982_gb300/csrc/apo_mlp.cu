@@ -9,6 +9,8 @@
 // from the archive.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "apo_internal.h"
 #include "apo_mlp.h"
 
@@ -187,8 +189,13 @@ __device__ __forceinline__ void tc_store(unsigned char* As, unsigned char* Bs, c
     }
 }
 
+// With ws (split K), CTA z of the grid's z dimension accumulates only the K
+// chunks [z cps, (z + 1) cps) and writes its raw fp32 tile to ws[z][M][N];
+// splitk_epilogue_kernel then sums the slices in order and applies the
+// epilogue.  Without ws, cps covers all of K and the epilogue is fused.
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(kTThreads) gemm_bf16_tc_kernel(GemmArgs g, bool va, bool vb, int* err)
+__global__ void __launch_bounds__(kTThreads) gemm_bf16_tc_kernel(GemmArgs g, bool va, bool vb, int cps, float* ws,
+                                                                 int* err)
 {
     extern __shared__ __align__(128) unsigned char gsm[];
     __shared__ __align__(8) unsigned long long mbar[2];
@@ -214,11 +221,15 @@ __global__ void __launch_bounds__(kTThreads) gemm_bf16_tc_kernel(GemmArgs g, boo
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" : : : "memory");
     const uint32_t tmem = tmem_slot;
-    const int nch = (g.K + kTK - 1) / kTK;
+    // this CTA's K chunks: c0 .. c0 + nch - 1 (K bounded to their end)
+    const int c0 = blockIdx.z * cps;
+    const int nch = max(0, min((g.K + kTK - 1) / kTK - c0, cps));
+    GemmArgs gk = g;
+    gk.K = min(g.K, (c0 + nch) * kTK);
     bool ok = true;
     uint4 ra[kGA], rb[kGB];
     if (nch > 0) {
-        tc_load<TA, TB>(g, m0, n0, 0, va, vb, ra, rb);
+        tc_load<TA, TB>(gk, m0, n0, c0 * kTK, va, vb, ra, rb);
         tc_store<TA, TB>(As[0], Bs[0], ra, rb);
         asm volatile("fence.proxy.async.shared::cta;" : : : "memory");
         __syncthreads();
@@ -245,7 +256,7 @@ __global__ void __launch_bounds__(kTThreads) gemm_bf16_tc_kernel(GemmArgs g, boo
         }
         if (c + 1 < nch) {
             const int nb = (c + 1) & 1;
-            tc_load<TA, TB>(g, m0, n0, (c + 1) * kTK, va, vb, ra, rb);   // in flight during the MMAs
+            tc_load<TA, TB>(gk, m0, n0, (c0 + c + 1) * kTK, va, vb, ra, rb);   // in flight during the MMAs
             // the MMAs of chunk c - 1 read buffer nb
             if (c >= 1 && !mbar_wait(mb[nb], (uint32_t)((c - 1) >> 1) & 1u)) ok = false;
             tc_store<TA, TB>(As[nb], Bs[nb], ra, rb);
@@ -284,6 +295,16 @@ __global__ void __launch_bounds__(kTThreads) gemm_bf16_tc_kernel(GemmArgs g, boo
         for (int j = 0; j < 16; ++j) tile[rl * kTS + 16 * cg + j] = __uint_as_float(r[j]);
     }
     __syncthreads();
+    // split K: the raw tile goes to this CTA's slice of the workspace
+    GemmArgs ge = g;
+    if (ws) {
+        ge.bias = nullptr;
+        ge.mask = nullptr;
+        ge.relu = 0;
+        ge.Cb = nullptr;
+        ge.Cf = ws + (size_t)blockIdx.z * g.M * g.N;
+        ge.ldc = g.N;
+    }
     if (ok) {
         // 8 elements per thread at a time: their bias and mask loads are all
         // issued before any result is stored (the outputs could alias them)
@@ -296,8 +317,8 @@ __global__ void __launch_bounds__(kTThreads) gemm_bf16_tc_kernel(GemmArgs g, boo
                 const int rr = i / kTN, cc = i - rr * kTN;
                 const int m = m0 + rr, n = n0 + cc;
                 const bool in = i < kTM * kTN && m < g.M && n < g.N;
-                bv[u] = (in && g.bias) ? __ldg(g.bias + n) : 0.f;
-                mv[u] = (in && g.mask) ? __ldg(g.mask + (size_t)m * g.ldm + n) : 1.f;
+                bv[u] = (in && ge.bias) ? __ldg(ge.bias + n) : 0.f;
+                mv[u] = (in && ge.mask) ? __ldg(ge.mask + (size_t)m * ge.ldm + n) : 1.f;
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
@@ -306,10 +327,10 @@ __global__ void __launch_bounds__(kTThreads) gemm_bf16_tc_kernel(GemmArgs g, boo
                 const int m = m0 + rr, n = n0 + cc;
                 if (i >= kTM * kTN || m >= g.M || n >= g.N) continue;
                 float v = tile[rr * kTS + cc] + bv[u];
-                if (g.mask) v = mv[u] > 0.f ? v : 0.f;
-                if (g.relu) v = fmaxf(v, 0.f);
-                if (g.Cf) g.Cf[(size_t)m * g.ldc + n] = v;
-                if (g.Cb) g.Cb[(size_t)m * g.ldcb + n] = __float2bfloat16(v);
+                if (ge.mask) v = mv[u] > 0.f ? v : 0.f;
+                if (ge.relu) v = fmaxf(v, 0.f);
+                if (ge.Cf) ge.Cf[(size_t)m * ge.ldc + n] = v;
+                if (ge.Cb) ge.Cb[(size_t)m * ge.ldcb + n] = __float2bfloat16(v);
             }
         }
     }
@@ -318,6 +339,23 @@ __global__ void __launch_bounds__(kTThreads) gemm_bf16_tc_kernel(GemmArgs g, boo
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" : : "r"(tmem), "r"(kTN) : "memory");
     if (!ok && tid == 0) atomicCAS(err, 0, 4 /* APO_ERR_TIMEOUT */);
+}
+
+// Sum of the ksplit slices of ws (in slice order) and the epilogue of
+// gemm_bf16_tc_kernel: bias, ReLU-derivative mask, ReLU, fp32 / bf16 outputs.
+__global__ void splitk_epilogue_kernel(GemmArgs g, const float* __restrict__ ws, int ksplit)
+{
+    const size_t MN = (size_t)g.M * g.N;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN; i += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i / g.N), n = (int)(i - (size_t)m * g.N);
+        float v = 0.f;
+        for (int z = 0; z < ksplit; ++z) v += ws[(size_t)z * MN + i];
+        v += g.bias ? g.bias[n] : 0.f;
+        if (g.mask) v = g.mask[(size_t)m * g.ldm + n] > 0.f ? v : 0.f;
+        if (g.relu) v = fmaxf(v, 0.f);
+        if (g.Cf) g.Cf[(size_t)m * g.ldc + n] = v;
+        if (g.Cb) g.Cb[(size_t)m * g.ldcb + n] = __float2bfloat16(v);
+    }
 }
 
 // C(m, n) = sum_k A(m, k) B(k, n), A(m, k) = TA ? A[k lda + m] : A[m lda + k],
@@ -341,11 +379,45 @@ cudaError_t gemm_bf16(const GemmArgs& g, bool ta, bool tb, cudaStream_t st)
         cudaFuncSetAttribute(gemm_bf16_tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
         attr_set = true;
     }
-    dim3 grid((g.N + kTN - 1) / kTN, (g.M + kTM - 1) / kTM);
-    if (!ta && !tb) gemm_bf16_tc_kernel<false, false><<<grid, kTThreads, kTcSmem, st>>>(g, va, vb, err);
-    else if (ta && !tb) gemm_bf16_tc_kernel<true, false><<<grid, kTThreads, kTcSmem, st>>>(g, va, vb, err);
-    else if (!ta && tb) gemm_bf16_tc_kernel<false, true><<<grid, kTThreads, kTcSmem, st>>>(g, va, vb, err);
-    else gemm_bf16_tc_kernel<true, true><<<grid, kTThreads, kTcSmem, st>>>(g, va, vb, err);
+    // Few output tiles (the network's layers make 8 to 16) leave most SMs
+    // idle while each CTA walks K chunk by chunk, so K is split until about
+    // kSplitTarget CTAs run; the slices are summed in a fixed order by the
+    // epilogue kernel (deterministic).  The workspace is one device buffer,
+    // grown when needed: calls are serial on the caller's stream.
+    constexpr int kSplitTarget = 128;
+    const int tiles = ((g.N + kTN - 1) / kTN) * ((g.M + kTM - 1) / kTM);
+    const int nch = (g.K + kTK - 1) / kTK;
+    int cps = nch > 0 ? nch : 1, ksplit = 1;
+    if (nch > 1 && tiles < kSplitTarget) {
+        const int want = std::min(nch, std::max(1, kSplitTarget / tiles));
+        cps = (nch + want - 1) / want;
+        ksplit = (nch + cps - 1) / cps;
+    }
+    float* ws = nullptr;
+    if (ksplit > 1) {
+        static float* s_ws = nullptr;
+        static size_t s_ws_elems = 0;
+        const size_t need = (size_t)ksplit * g.M * g.N;
+        if (need > s_ws_elems) {
+            if (s_ws) cudaFree(s_ws);
+            s_ws = nullptr;
+            s_ws_elems = 0;
+            const cudaError_t e = cudaMalloc(&s_ws, need * sizeof(float));
+            if (e != cudaSuccess) return e;
+            s_ws_elems = need;
+        }
+        ws = s_ws;
+    }
+    dim3 grid((g.N + kTN - 1) / kTN, (g.M + kTM - 1) / kTM, ksplit);
+    if (!ta && !tb) gemm_bf16_tc_kernel<false, false><<<grid, kTThreads, kTcSmem, st>>>(g, va, vb, cps, ws, err);
+    else if (ta && !tb) gemm_bf16_tc_kernel<true, false><<<grid, kTThreads, kTcSmem, st>>>(g, va, vb, cps, ws, err);
+    else if (!ta && tb) gemm_bf16_tc_kernel<false, true><<<grid, kTThreads, kTcSmem, st>>>(g, va, vb, cps, ws, err);
+    else gemm_bf16_tc_kernel<true, true><<<grid, kTThreads, kTcSmem, st>>>(g, va, vb, cps, ws, err);
+    if (ksplit > 1) {
+        const size_t MN = (size_t)g.M * g.N;
+        const int blocks = (int)std::min<size_t>((MN + 255) / 256, 1024);
+        splitk_epilogue_kernel<<<blocks, 256, 0, st>>>(g, ws, ksplit);
+    }
     return cudaGetLastError();
 }
 
