@@ -530,6 +530,7 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
                 const int i = base + tid / tpk;
                 const KT k = i < nown ? keys[i] : KO::pad();
                 int rk = 0;
+#pragma unroll 8
                 for (int j = sub; j < nown; j += tpk) rk += KO::less(keys[j], k) ? 1 : 0;
                 for (int m = 1; m < tpk; m <<= 1) rk += __shfl_xor_sync(0xffffffffu, rk, m);
                 if (sub == 0 && i < nown) {
