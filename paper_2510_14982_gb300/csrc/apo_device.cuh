@@ -96,9 +96,11 @@ __host__ __device__ __forceinline__ int split_words(int D)
 
 // The tcgen05 rotation of the cooperative grid kernel: UMMA M = kTcM output
 // dimensions (the rotation rows, D <= kTcM), N = kTcN candidate rows of a
-// chunk (the accumulator's TMEM columns).
+// chunk (the accumulator's TMEM columns; a CTA of 38 per run at ps 4096 owns
+// 108 rows, one chunk).  kTcCols TMEM columns are allocated (a power of two).
 constexpr int kTcM = 128;
-constexpr int kTcN = 64;
+constexpr int kTcN = 112;
+constexpr int kTcCols = 128;
 
 // Byte offset of element (r, k) of a K-major operand with Kt columns (a
 // multiple of 16) in the canonical UMMA layout without swizzle: core

@@ -25,8 +25,10 @@ inline int plan_pow2(int v)
 // after it TY, the chunk's split candidates (kTcN x Np each).  The MMAs read
 // kTcM rotation rows; rows Np..kTcM-1 of the lo part fall into TY (never
 // beyond it, since (kTcM - Np) Np 2 <= 4 kTcN Np) and only produce
-// accumulator rows that are not read.
-static_assert(kGridChunk == kTcN, "the tcgen05 rotation takes a whole grid chunk per MMA");
+// accumulator rows that are not read.  A tc plan takes kTcN-row chunks, and
+// the Z tile (kTcN x Np fp32, the same bytes as TY) shares TY's space: it is
+// written only after the chunk's MMAs have completed.
+static_assert(4 * kTcN >= 2 * kTcM, "the rotation rows read past Np must stay inside TY");
 inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool mt_smem, bool grid,
                                int chunk = 0, bool tc = false)
 {
@@ -70,7 +72,7 @@ inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool
     L.Xc = take(ch * Dp * 4);
     L.Xo = take(grid ? 0 : ch * Dp * 4);                // grid mode copies no unchanged rows
     L.Yc = take(any_plain ? ch * Dp * 4 : 0);          // transposed: [Dp][chunk]
-    L.Zc = take(P->any_rot ? ch * Np * 4 : 0);          // [chunk][Np]
+    L.Zc = tc ? L.TY : take(P->any_rot ? ch * Np * 4 : 0);   // [chunk][Np]
     L.rowF = take(2 * ch * fsz);   // new fitness | old fitness of the chunk rows
     L.compG = take(P->ncomp > 1 ? ch * kMaxComp * 4 : 0);
     L.compA = take(P->ncomp > 1 ? ch * kMaxComp * 4 : 0);
@@ -90,7 +92,7 @@ inline SmemPlan choose_plan(const apo_problem* P, int ps, bool resident, bool gr
     const bool can = P->ncomp == 1 && P->dev.comp[0].MT;
     if (grid && can && P->dev.comp[0].Th) {
         // the grid kernel's rotation on tcgen05
-        SmemPlan L = make_smem_plan(P, ps, resident, false, grid, kGridChunk, true);
+        SmemPlan L = make_smem_plan(P, ps, resident, false, grid, kTcN, true);
         if (L.total <= smem_max) return L;
     }
     if (can) {

@@ -27,7 +27,7 @@ constexpr uint32_t kRotIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uin
 constexpr unsigned long long kMmaTimeoutNs = 1000000000ull;   // 1 s per wait
 
 struct TcState {
-    uint32_t tmem;    // accumulator: kTcN columns x kTcM lanes
+    uint32_t tmem;    // accumulator: kTcN of kTcCols columns x kTcM lanes
     uint32_t mbar;    // shared address of the completion mbarrier
     uint32_t phase;   // commits waited for so far
 };
@@ -49,7 +49,7 @@ __device__ __forceinline__ void tc_setup(TcState& st, uint32_t* tmem_slot, unsig
     if ((threadIdx.x >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :
-                     : "r"((uint32_t)__cvta_generic_to_shared(tmem_slot)), "r"(kTcN)
+                     : "r"((uint32_t)__cvta_generic_to_shared(tmem_slot)), "r"(kTcCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" : : : "memory");
     }
@@ -70,7 +70,7 @@ __device__ __forceinline__ void tc_teardown(const TcState& st)
     asm volatile("tcgen05.fence::before_thread_sync;" : : : "memory");
     __syncthreads();
     if ((threadIdx.x >> 5) == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" : : "r"(st.tmem), "r"(kTcN)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" : : "r"(st.tmem), "r"(kTcCols)
                      : "memory");
 }
 
