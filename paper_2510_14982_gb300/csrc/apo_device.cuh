@@ -14,7 +14,8 @@ constexpr int kThreads = 256;     // threads per CTA of the work-queue (resident
 constexpr int kWarps = kThreads / 32;
 constexpr int kGridThreads = 512; // threads per CTA of the cooperative grid kernel
 constexpr int kMaxWarps = kGridThreads / 32;
-constexpr int kChunk = 32;        // candidate rows evaluated together (resident mode)
+constexpr int kChunk = 32;        // candidate rows evaluated together when larger chunks do not fit
+constexpr int kQueueChunk = 64;   // candidate rows evaluated together (work-queue mode)
 constexpr int kGridChunk = 64;    // candidate rows evaluated together (grid mode)
 constexpr int kMaxComp = 10;      // composition components
 constexpr int kMaxGridCtas = 1024; // CTAs cooperating on one run (grid mode)

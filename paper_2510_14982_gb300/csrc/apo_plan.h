@@ -19,7 +19,7 @@ inline int plan_pow2(int v)
 
 // Layout for a run of population ps (0 for the evaluation hooks).  grid
 // selects the cooperative-grid layout (512 threads, 64-row chunks);
-// otherwise the resident / work-queue layout (256 threads, 32-row chunks).
+// otherwise the resident / work-queue layout (256 threads, 64-row chunks).
 // tc (grid only) places the tcgen05 rotation operands: TA, the rotation's
 // fp16 hi and lo parts (Np x Np each, canonical UMMA layout), then directly
 // after it TY, the chunk's split candidates (kTcN x Np each).  The MMAs read
@@ -40,7 +40,7 @@ inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool
     L.ps_pad = ps > 0 ? plan_pow2(ps) : 0;
     L.resident = resident;
     L.mt_smem = mt_smem;
-    L.chunk = chunk > 0 ? chunk : (grid ? kGridChunk : kChunk);
+    L.chunk = chunk > 0 ? chunk : (grid ? kGridChunk : kQueueChunk);
     L.threads = grid ? kGridThreads : kThreads;
     // rotated components are evaluated on the tensor cores from the row-major
     // candidates; only an unrotated one needs the transposed copy Yc
@@ -95,13 +95,19 @@ inline SmemPlan choose_plan(const apo_problem* P, int ps, bool resident, bool gr
         SmemPlan L = make_smem_plan(P, ps, resident, false, grid, kTcN, true);
         if (L.total <= smem_max) return L;
     }
-    if (can) {
-        SmemPlan L = make_smem_plan(P, ps, resident, true, grid);
+    // the mode's chunk (64 rows), else 32-row chunks; the rotation in shared
+    // memory when that fits too (results do not depend on the layout)
+    const int chunks[2] = {grid ? kGridChunk : kQueueChunk, kChunk};
+    SmemPlan L{};
+    for (int c : chunks) {
+        if (can) {
+            L = make_smem_plan(P, ps, resident, true, grid, c);
+            if (L.total <= smem_max) return L;
+        }
+        L = make_smem_plan(P, ps, resident, false, grid, c);
         if (L.total <= smem_max) return L;
     }
-    SmemPlan L = make_smem_plan(P, ps, resident, false, grid);
-    if (grid && L.total > smem_max) L = make_smem_plan(P, ps, resident, false, grid, kChunk);   // 32-row chunks
-    return L;
+    return L;   // does not fit: the caller reports it
 }
 
 }  // namespace apo
