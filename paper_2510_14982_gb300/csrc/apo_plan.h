@@ -87,7 +87,9 @@ inline SmemPlan make_smem_plan(const apo_problem* P, int ps, bool resident, bool
 
 // The rotation of a single-component objective stays in shared memory when
 // the whole layout still fits.
-inline SmemPlan choose_plan(const apo_problem* P, int ps, bool resident, bool grid, size_t smem_max)
+// chunk0 > 0 replaces the mode's chunk (kernels whose grid is one CTA per
+// chunk keep small chunks for parallelism).
+inline SmemPlan choose_plan(const apo_problem* P, int ps, bool resident, bool grid, size_t smem_max, int chunk0 = 0)
 {
     const bool can = P->ncomp == 1 && P->dev.comp[0].MT;
     if (grid && can && P->dev.comp[0].Th) {
@@ -97,7 +99,7 @@ inline SmemPlan choose_plan(const apo_problem* P, int ps, bool resident, bool gr
     }
     // the mode's chunk (64 rows), else 32-row chunks; the rotation in shared
     // memory when that fits too (results do not depend on the layout)
-    const int chunks[2] = {grid ? kGridChunk : kQueueChunk, kChunk};
+    const int chunks[2] = {chunk0 > 0 ? chunk0 : (grid ? kGridChunk : kQueueChunk), kChunk};
     SmemPlan L{};
     for (int c : chunks) {
         if (can) {

@@ -653,7 +653,7 @@ extern "C" apo_status apo_surrogate_candidates(const apo_problem* P, const apo_p
     const int ps = p->ps, T = p->max_iter, D = P->D, Dp = P->Dp;
     const int ps_pad = plan_pow2(ps);
     const int qpl = D <= 64 ? 1 : (D <= 128 ? 2 : 4);
-    const SmemPlan plan = choose_plan(P, ps, false, false, 232448 - 2048);
+    const SmemPlan plan = choose_plan(P, ps, false, false, 232448 - 2048, kChunk);   // one CTA per chunk
     const int W = (ps + 31) / 32;
     size_t off = 0;
     auto take = [&](size_t bytes) { off = (off + 255) / 256 * 256; const size_t at = off; off += bytes; return at; };
@@ -757,7 +757,7 @@ extern "C" apo_status apo_run_surrogate(const apo_problem* P, const apo_params* 
         refresh_bf16(M, 0);
     }
     const int Kp = M->Kp;
-    const SmemPlan plan = choose_plan(P, ps, false, false, 232448 - 2048);
+    const SmemPlan plan = choose_plan(P, ps, false, false, 232448 - 2048, kChunk);   // one CTA per chunk
 
     // workspace
     const int W = (ps + 31) / 32;
