@@ -64,6 +64,35 @@ int main()
     apo_problem B = make(200, 1, true, false);
     CHECK(!choose_plan(&B, 4096, false, true, smem_max).tc, "D 200 got a tcgen05 plan");
 
+    // work-queue plans: 64-row chunks when they fit the budget, else 32-row
+    // ones; a preferred chunk is honoured; nothing that fits with 32-row
+    // chunks is refused
+    int q64 = 0, q32 = 0;
+    for (int D : {10, 20, 50, 100, 200}) {
+        for (int ps : {20, 77, 300, 512, 1024}) {
+            for (size_t budget : {(size_t)56 * 1024, (size_t)75 * 1024, (size_t)113 * 1024, smem_max}) {
+                for (bool res : {true, false}) {
+                    apo_problem P = make(D, 1, true, false);
+                    const SmemPlan L = choose_plan(&P, ps, res, false, budget);
+                    const SmemPlan S32 = make_smem_plan(&P, ps, res, false, false, kChunk);
+                    if (L.total <= budget) {
+                        CHECK(L.chunk == kQueueChunk || L.chunk == kChunk, "D %d ps %d: chunk %d", D, ps, L.chunk);
+                        if (L.chunk == kChunk)
+                            CHECK(make_smem_plan(&P, ps, res, false, false, kQueueChunk).total > budget,
+                                  "D %d ps %d: 32-row chunks although 64 fit", D, ps);
+                        q64 += L.chunk == kQueueChunk;
+                        q32 += L.chunk == kChunk;
+                    } else {
+                        CHECK(S32.total > budget, "D %d ps %d res %d: refused although 32-row chunks fit", D, ps, (int)res);
+                    }
+                    const SmemPlan Lp = choose_plan(&P, ps, res, false, budget, kChunk);
+                    if (Lp.total <= budget) CHECK(Lp.chunk == kChunk, "D %d ps %d: preferred chunk ignored", D, ps);
+                }
+            }
+        }
+    }
+    CHECK(q64 > 0 && q32 > 0, "work-queue plans: %d with 64-row and %d with 32-row chunks", q64, q32);
+
     // canonical K-major layout: a bijection onto the operand's bytes, 8-row x
     // 16-byte core matrices, K-adjacent ones 128 bytes apart (the descriptor's
     // leading offset), 8-row groups Kt * 16 bytes apart (its stride offset)
