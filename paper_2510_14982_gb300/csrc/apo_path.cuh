@@ -295,21 +295,23 @@ __device__ __forceinline__ void seg_values(const float* const (&z)[NR], const De
 }
 
 // Objective of the rows [0, rows) of the Z tile (rows Np apart) into rowF:
-// warp w takes rows w, w + nw, w + 2 nw, w + 3 nw together.
+// warp w takes rows w, w + nw, ..., w + 7 nw together (one pass for up to
+// 8 nw rows).
 template <typename FitT>
 __device__ __forceinline__ void zrows_to_f(const Smem<FitT>& S, const DevComp& C, int D, int Np, int rows)
 {
+    constexpr int NR = 8;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int r0 = warp; r0 < rows; r0 += 4 * nw) {
+    for (int r0 = warp; r0 < rows; r0 += NR * nw) {
         // rows past the last one repeat it (computed, not stored)
-        const float* z[4];
+        const float* z[NR];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) z[i] = S.Zc + (size_t)min(r0 + i * nw, rows - 1) * Np;
-        float f[4];
-        seg_values<4>(z, C, S.ew, D, f);
+        for (int i = 0; i < NR; ++i) z[i] = S.Zc + (size_t)min(r0 + i * nw, rows - 1) * Np;
+        float f[NR];
+        seg_values<NR>(z, C, S.ew, D, f);
         if (lane == 0)
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < NR; ++i)
                 if (r0 + i * nw < rows) S.rowF[r0 + i * nw] = (FitT)f[i];
     }
 }
