@@ -18,8 +18,9 @@ inline int plan_pow2(int v)
 }
 
 // Layout for a run of population ps (0 for the evaluation hooks).  grid
-// selects the cooperative-grid layout (512 threads, 64-row chunks);
-// otherwise the resident / work-queue layout (256 threads, 64-row chunks).
+// selects the cooperative-grid layout (512 threads, 64-row chunks, kTcN rows
+// with tc); otherwise the resident / work-queue layout (256 threads, 64-row
+// chunks).  An explicit chunk overrides the default.
 // tc (grid only) places the tcgen05 rotation operands: TA, the rotation's
 // fp16 hi and lo parts (Np x Np each, canonical UMMA layout), then directly
 // after it TY, the chunk's split candidates (kTcN x Np each).  The MMAs read
