@@ -20,7 +20,8 @@
  *   R1  `rand` is one uniform draw per protozoon, `Rand` one per dimension,
  *       `+-` one random sign per protozoon.
  *   R2  j, k-, k+ (autotrophic mode, Eq. 6-7) are independent uniform ranks
- *       over the whole population.                      -- parity unpinned
+ *       over the whole population (the paper prints no draws; pinned by a
+ *       statistical test that reads them off unit-vector populations).
  *   R3  X_{i-k}, X_{i+k} (Eq. 8, 10) clamp to ranks 1..ps.
  *   R4  eps (Eq. 7, 10) = 2^-52.
  *   R5  p_dr (Eq. 13) as printed, with the minus sign (pdr_form 0); the

@@ -195,3 +195,65 @@ def test_apo_minimises_the_sphere(orc):
     prm = orc.params(ps=30, pf_max=0.1, max_iter=300, seed=1)
     _, bf, curve = orc.apo_run(p, prm)
     assert bf < 1e-3 * curve[0]
+
+
+def test_autotrophic_partners_are_independent_uniform_ranks(orc):
+    """Reading R2: in the autotrophic mode (Eq. 6-7) j and the pair k-, k+ are
+    independent uniform ranks over the whole population.  With rows X_r = e_r
+    (D = ps), equal fitness (w = exp(-1) for every pair, Eq. 7) and every
+    dimension of the last-ranked protozoon masked (ceil(D ps / ps) = D, Eq. 5),
+    its candidate minus X_i is f (e_j - e_i) + f w (e_a - e_b), so j, a, b can be
+    read off.  Over many seeds they must be uniform and independent (a mistake
+    such as taking rank neighbours, or one draw for two of them, fails)."""
+    chi2 = pytest.importorskip("scipy.stats").chi2
+    ps = D = 32
+    prob = orc.OracleProblem(inputs.OBJ_SPHERE, D, -10.0, 10.0)
+    X = np.eye(ps)
+    F = np.ones(ps)
+    w = np.exp(-1.0)
+    i = ps - 1
+    js, as_, bs = [], [], []
+    n_two_f = n_two_fw = 0
+    N = 3000
+    for seed in range(N):
+        prm = orc.params(ps, 1, 0.0, 100000, seed)
+        _, _, info = orc.apo_step(prob, prm, 1, X, F, with_info=True)
+        assert np.array_equal(info["order"], np.arange(ps))
+        assert info["mode"][i] == 2 and info["mask"][i].all()
+        delta = info["xnew_raw"][i] - X[i]
+        nz = np.flatnonzero(np.abs(delta) > 1e-12)
+        f = -delta[i]
+        if len(nz) == 4 and f > 0:
+            rest = [d for d in nz if d != i]
+            vals = {d: delta[d] / f for d in rest}
+            j = [d for d in rest if abs(vals[d] - 1.0) < 1e-9]
+            a = [d for d in rest if abs(vals[d] - w) < 1e-9]
+            b = [d for d in rest if abs(vals[d] + w) < 1e-9]
+            assert len(j) == len(a) == len(b) == 1, (seed, vals)
+            js.append(j[0]); as_.append(a[0]); bs.append(b[0])
+        elif len(nz) == 2:
+            ratio = delta[nz].max() / -delta[nz].min()
+            assert abs(ratio - 1.0) < 1e-9, (seed, delta[nz])
+            if i in nz:
+                n_two_f += 1      # a == b: only f (e_j - e_i) remains
+            else:
+                n_two_fw += 1     # j == i: only f w (e_a - e_b) remains
+    clean = len(js)
+    # all four distinct with probability (31/32)(30/32)(29/32)
+    assert abs(clean / N - 31 * 30 * 29 / 32 ** 3) < 0.03, clean
+    # a == b and j == i each happen with probability about 1/ps
+    for n in (n_two_f, n_two_fw):
+        assert 0.5 * N / ps < n < 1.6 * N / ps, (n_two_f, n_two_fw)
+    # in the clean samples each of j, a, b is uniform over the 31 ranks other than i
+    crit = chi2.ppf(1.0 - 1e-6, ps - 2)
+    for v in (js, as_, bs):
+        counts = np.bincount(v, minlength=ps)[:ps - 1]
+        expected = clean / (ps - 1)
+        assert ((counts - expected) ** 2 / expected).sum() < crit
+    # and j, a are independent: (j mod 4, a mod 4) over 16 cells, up to the
+    # small dependence that distinctness induces (same-cell pairs are 1/30 rarer)
+    cells = np.zeros((4, 4))
+    for j, a in zip(js, as_):
+        cells[j % 4, a % 4] += 1
+    expected = np.outer(cells.sum(1), cells.sum(0)) / clean
+    assert ((cells - expected) ** 2 / expected).sum() < chi2.ppf(1.0 - 1e-6, 9)
