@@ -257,3 +257,32 @@ def test_autotrophic_partners_are_independent_uniform_ranks(orc):
         cells[j % 4, a % 4] += 1
     expected = np.outer(cells.sum(1), cells.sum(0)) / clean
     assert ((cells - expected) ** 2 / expected).sum() < chi2.ppf(1.0 - 1e-6, 9)
+
+
+def test_heterotrophic_neighbours_clamp_at_the_last_rank(orc):
+    """Reading R3: X_{i-k}, X_{i+k} (Eq. 8, 10) clamp to ranks 1..ps.  With rows
+    X_r = e_r (D = ps), equal fitness and the last rank fully masked (Eq. 5),
+    its heterotrophic candidate minus X_i is f (x_near - x_i) + f w (e_{ps-2} -
+    e_{ps-1}): x_near (Eq. 9) moves only dimension ps-1, and the clamped k+ is
+    the protozoon itself.  So only dimensions ps-2 and ps-1 change, dimension
+    ps-2 by +f w.  Wrapping k+ around to rank 1 would move dimension 0;
+    reflecting it to rank ps-1 would cancel the e_{ps-2} term."""
+    ps = D = 16
+    prob = orc.OracleProblem(inputs.OBJ_SPHERE, D, -10.0, 10.0)
+    X = np.eye(ps)
+    F = np.ones(ps)
+    i = ps - 1
+    seen = 0
+    for seed in range(200):
+        # t = T - 1: heterotrophic with probability 1 - p_ah(t) close to 1 (Eq. 12),
+        # and the foraging factor f (Eq. 4) is small but not zero
+        prm = orc.params(ps, 1, 0.0, 100, seed)
+        _, _, info = orc.apo_step(prob, prm, 99, X, F, with_info=True)
+        if info["mode"][i] != 3:
+            continue
+        seen += 1
+        assert info["mask"][i].all()
+        delta = info["xnew_raw"][i] - X[i]
+        assert np.all(delta[:ps - 2] == 0.0), (seed, delta)
+        assert delta[ps - 2] > 0.0, (seed, delta)
+    assert seen > 150
