@@ -382,8 +382,8 @@ cudaError_t gemm_bf16(const GemmArgs& g, bool ta, bool tb, cudaStream_t st)
     // Few output tiles (the network's layers make 8 to 16) leave most SMs
     // idle while each CTA walks K chunk by chunk, so K is split until about
     // kSplitTarget CTAs run; the slices are summed in a fixed order by the
-    // epilogue kernel (deterministic).  The workspace is one device buffer,
-    // grown when needed: calls are serial on the caller's stream.
+    // epilogue kernel (deterministic).  The slices go to the caller's
+    // workspace (g.ws); without one, or when it is too small, K is not split.
     constexpr int kSplitTarget = 128;
     const int tiles = ((g.N + kTN - 1) / kTN) * ((g.M + kTM - 1) / kTM);
     const int nch = (g.K + kTK - 1) / kTK;
@@ -393,21 +393,11 @@ cudaError_t gemm_bf16(const GemmArgs& g, bool ta, bool tb, cudaStream_t st)
         cps = (nch + want - 1) / want;
         ksplit = (nch + cps - 1) / cps;
     }
-    float* ws = nullptr;
-    if (ksplit > 1) {
-        static float* s_ws = nullptr;
-        static size_t s_ws_elems = 0;
-        const size_t need = (size_t)ksplit * g.M * g.N;
-        if (need > s_ws_elems) {
-            if (s_ws) cudaFree(s_ws);
-            s_ws = nullptr;
-            s_ws_elems = 0;
-            const cudaError_t e = cudaMalloc(&s_ws, need * sizeof(float));
-            if (e != cudaSuccess) return e;
-            s_ws_elems = need;
-        }
-        ws = s_ws;
+    if (ksplit > 1 && (!g.ws || (size_t)ksplit * g.M * g.N > g.ws_elems)) {
+        ksplit = 1;
+        cps = nch > 0 ? nch : 1;
     }
+    float* ws = ksplit > 1 ? g.ws : nullptr;
     dim3 grid((g.N + kTN - 1) / kTN, (g.M + kTM - 1) / kTM, ksplit);
     if (!ta && !tb) gemm_bf16_tc_kernel<false, false><<<grid, kTThreads, kTcSmem, st>>>(g, va, vb, cps, ws, err);
     else if (ta && !tb) gemm_bf16_tc_kernel<true, false><<<grid, kTThreads, kTcSmem, st>>>(g, va, vb, cps, ws, err);

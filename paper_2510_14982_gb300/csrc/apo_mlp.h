@@ -25,7 +25,14 @@ struct GemmArgs {
     int ldc;
     __nv_bfloat16* Cb;   // bf16 output or nullptr
     int ldcb;
+    float* ws;           // split-K workspace owned by the caller, or nullptr (no split)
+    size_t ws_elems;     // its size in floats; kSplitWsElems covers every shape
 };
+
+// Split K runs only with fewer than 128 output tiles of 128 x 64, and then
+// ksplit M N <= 128 (128 x 64): one workspace of this many floats serves
+// every GEMM shape.
+constexpr size_t kSplitWsElems = (size_t)128 * 128 * 64;
 
 cudaError_t gemm_bf16(const GemmArgs& g, bool ta, bool tb, cudaStream_t st);
 cudaError_t launch_out_layer(int M, int K, const __nv_bfloat16* H, const __nv_bfloat16* w, const float* b, float* y,

@@ -78,6 +78,7 @@ struct apo_mlp {
     __nv_bfloat16 *Xb, *H1b, *H2b, *dZ2b, *dZ1b;
     float *Z1, *Z2, *dZ2, *dZ1, *y, *t, *dy, *loss;
     int* idx;
+    float* ws;        // split-K workspace of the GEMMs (kSplitWsElems floats)
     void* mem;
 };
 
@@ -111,6 +112,7 @@ apo_status mlp_alloc(apo_mlp* M, int cap)
     float** fr[] = {&M->y, &M->t, &M->dy};
     for (auto p : fr) add((void**)p, (size_t)cap * 4);
     add((void**)&M->idx, (size_t)cap * 4);
+    add((void**)&M->ws, kSplitWsElems * 4);
     for (auto& it : items) off = (off + 255) / 256 * 256 + it.second;
     SUR_CUDA(cudaMalloc(&M->mem, off));
     SUR_CUDA(cudaMemset(M->mem, 0, off));
@@ -144,6 +146,8 @@ apo_status mlp_forward_rows(apo_mlp* M, int n, cudaStream_t st)
 {
     GemmArgs g;
     std::memset(&g, 0, sizeof(g));
+    g.ws = M->ws;
+    g.ws_elems = kSplitWsElems;
     g.M = n; g.N = kH; g.K = M->Kp; g.A = M->Xb; g.lda = M->Kp; g.B = M->W1b; g.ldb = kH;
     g.bias = M->b1; g.relu = 1; g.Cf = M->Z1; g.ldc = kH; g.Cb = M->H1b; g.ldcb = kH;
     SUR_CUDA(gemm_bf16(g, false, false, st));
@@ -164,17 +168,23 @@ apo_status mlp_backward_rows(apo_mlp* M, int n, cudaStream_t st)
     SUR_CUDA(launch_colsum(n, kH, M->dZ2, nullptr, nullptr, M->gb2, st)); // db2
     GemmArgs g;
     std::memset(&g, 0, sizeof(g));
+    g.ws = M->ws;
+    g.ws_elems = kSplitWsElems;
     // dW2 = H1^T dZ2
     g.M = kH; g.N = kH; g.K = n; g.A = M->H1b; g.lda = kH; g.B = M->dZ2b; g.ldb = kH; g.Cf = M->gW2; g.ldc = kH;
     SUR_CUDA(gemm_bf16(g, true, false, st));
     // dZ1 = (dZ2 W2^T) masked by Z1 > 0
     std::memset(&g, 0, sizeof(g));
+    g.ws = M->ws;
+    g.ws_elems = kSplitWsElems;
     g.M = n; g.N = kH; g.K = kH; g.A = M->dZ2b; g.lda = kH; g.B = M->W2b; g.ldb = kH;
     g.mask = M->Z1; g.ldm = kH; g.Cf = M->dZ1; g.ldc = kH; g.Cb = M->dZ1b; g.ldcb = kH;
     SUR_CUDA(gemm_bf16(g, false, true, st));
     SUR_CUDA(launch_colsum(n, kH, M->dZ1, nullptr, nullptr, M->gb1, st)); // db1
     // dW1 = X^T dZ1
     std::memset(&g, 0, sizeof(g));
+    g.ws = M->ws;
+    g.ws_elems = kSplitWsElems;
     g.M = M->Kp; g.N = kH; g.K = n; g.A = M->Xb; g.lda = M->Kp; g.B = M->dZ1b; g.ldb = kH; g.Cf = M->gW1; g.ldc = kH;
     SUR_CUDA(gemm_bf16(g, true, false, st));
     return APO_OK;
