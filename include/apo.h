@@ -42,7 +42,7 @@ typedef enum apo_status {
     APO_ERR_CUDA = 2,        /* a CUDA runtime call or a kernel launch failed   */
     APO_ERR_OOM = 3,         /* device or host allocation failed               */
     APO_ERR_TIMEOUT = 4,     /* a device-side wait exceeded its limit           */
-    APO_ERR_UNSUPPORTED = 5, /* valid, but outside what this build supports     */
+    APO_ERR_UNSUPPORTED = 5, /* valid, but outside what the library supports   */
     APO_ERR_INTERNAL = 6
 } apo_status;
 
