@@ -83,7 +83,8 @@ typedef struct apo_objective_desc {
 } apo_objective_desc;
 
 /* Algorithm 1 inputs.  Validation: ps >= 2, 1 <= np, 2*np < ps,
- * 0 <= pf_max <= 1, max_iter >= 1, pdr_form in {0, 1}. */
+ * 0 <= pf_max <= 1, max_iter >= 1 (or max_fes >= 2 ps), pdr_form and
+ * pair_policy in {0, 1}, max_fes >= 0. */
 typedef struct apo_params {
     int ps;           /* population size                                       */
     int np;           /* neighbour pairs in Eq. 6 and Eq. 8                     */
@@ -93,7 +94,22 @@ typedef struct apo_params {
     uint32_t run;     /* Philox key word 1 (independent stream per run)         */
     int pdr_form;     /* 0: Eq. 13 as printed, p_dr = (1 - cos((1-i/ps) pi))/2;
                          1: the mirrored (1 + cos((1-i/ps) pi))/2               */
+    int pair_policy;  /* the pairs (k-, k+) of Eq. 6-7 for rank i (1-based):
+                         0: independent uniform ranks over 1..ps;
+                         1: k- uniform over the ranks 1..i (at least as good
+                            as i), k+ uniform over i..ps (at most as good)     */
+    long long max_fes;/* 0: max_iter iterations.  > 0: an evaluation budget
+                         (MaxFEs counted in objective evaluations): ps at
+                         initialisation and ps per iteration, so the run takes
+                         T = floor(max_fes / ps) - 1 whole iterations and T is
+                         iter_max of Eq. 4, 9 and 12; max_iter is ignored.
+                         apo_effective_iterations() returns T.                  */
 } apo_params;
+
+/* The number of iterations a run with these params takes: max_iter, or the
+ * iterations that fit the evaluation budget max_fes (see apo_params); -1 when
+ * the params are invalid.  Size curves with it (+1 entry). */
+int apo_effective_iterations(const apo_params* params);
 
 typedef struct apo_problem apo_problem;
 
@@ -110,17 +126,18 @@ void apo_problem_destroy(apo_problem* prob);
 
 int apo_problem_dim(const apo_problem* prob);
 
-/* A whole run of Algorithm 1: initialisation, params->max_iter iterations of
+/* A whole run of Algorithm 1: initialisation, T = apo_effective_iterations()
+ * iterations (max_iter, or what the evaluation budget max_fes allows) of
  * sort, Dr selection (Eq. 11), dormancy / reproduction / autotrophic /
  * heterotrophic candidates (Eq. 1-10, 12-13), bound clamp, evaluation,
  * greedy replacement.  Outputs (host): best_x [D], *best_f, and curve
- * [max_iter + 1] (curve[t] = best fitness after iteration t, curve[0] after
+ * [T + 1] (curve[t] = best fitness after iteration t, curve[0] after
  * initialisation; NULL = not wanted).  Synchronous. */
 apo_status apo_run(const apo_problem* prob, const apo_params* params, void* stream,
                    float* best_x, double* best_f, float* curve);
 
 /* Same as apo_run with device outputs: d_best_x [D], d_best_f [1],
- * d_curve [max_iter + 1] or NULL.  Stream-ordered. */
+ * d_curve [T + 1] or NULL.  Stream-ordered. */
 apo_status apo_run_device(const apo_problem* prob, const apo_params* params, void* stream,
                           float* d_best_x, double* d_best_f, float* d_curve);
 
@@ -132,14 +149,19 @@ apo_status apo_run_device(const apo_problem* prob, const apo_params* params, voi
  * a deployment variant of apo_run_device with the same arguments and results.
  * It calls no cudaMalloc, cudaFree or allocating library routine: its
  * workspace is one file-scope device array of 8 MiB that every device loading
- * the library holds until the process exits, looked up on the first call on
- * each device (make that first call before any stream capture).  A run whose
- * workspace exceeds 8 MiB (roughly ps * D * 8 bytes when ps > 1024 or the
- * population does not fit in shared memory, plus (max_iter + 1) * ps / 8
- * bytes) is rejected with APO_ERR_UNSUPPORTED and a message naming the size.
- * Every call shares the array and clears what must start at zero; calls that
- * overlap on the GPU (other host threads or streams) race on it.  Returns
- * after the run has finished (synchronises `stream`). */
+ * the library holds until the process exits.  The array's device address is
+ * looked up (cudaGetSymbolAddress) by the first call made on each device and
+ * context, and again after a cudaDeviceReset; make that first call before any
+ * stream capture.  A run whose workspace exceeds 8 MiB is rejected with
+ * APO_ERR_UNSUPPORTED and a message naming the size.  The workspace is about
+ * 2 KB + ps * 4 + (T + 1) * (12 + 4 * ceil(ps / 32)) bytes, plus, when the run
+ * takes the cooperative grid kernel (ps >= 128) or its population does not
+ * fit in shared memory, ps * (8 * Dp + 8) bytes for the two population
+ * buffers (Dp = D rounded up to 4; Otsu: ps * (8 * Dp + 16)), plus, for the
+ * grid kernel, ps * 12 bytes of ranking buffers (Otsu: ps * 20).  Every call
+ * shares the array and clears what must start at zero; calls that overlap on
+ * the GPU (other host threads or streams) race on it.  Returns after the run
+ * has finished (synchronises `stream`). */
 apo_status apo_run_device_noalloc(const apo_problem* prob, const apo_params* params, void* stream,
                                   float* d_best_x, double* d_best_f, float* d_curve);
 
@@ -182,6 +204,31 @@ apo_status apo_batch_launch(apo_batch* batch, void* stream);
  * batch with it.  Writes the choice to *chosen when not NULL.  Synchronous. */
 apo_status apo_batch_autotune(apo_batch* batch, void* stream, int probe_iters, apo_batch_options* chosen);
 void apo_batch_destroy(apo_batch* batch);
+
+/* The initial population of a run (Algorithm 1 "Initialize": X_p = Xmin +
+ * U (Xmax - Xmin) with the INIT draws of protozoon p, F_p = f(X_p)), written
+ * to d_X [ps*D] and d_F [ps] (float64 for Otsu) in protozoon order: the state
+ * a run starts from, and the state apo_run_from_state(t_begin = 1) resumes.
+ * Stream-ordered. */
+apo_status apo_init_state(const apo_problem* prob, const apo_params* params, void* stream, float* d_X,
+                          void* d_F);
+
+/* Resume (checkpoint / restart): iterations t_begin..t_end (1 <= t_begin,
+ * t_begin - 1 <= t_end <= T, T = apo_effective_iterations(params), the
+ * iter_max of the schedules) of the run described by params, starting from
+ * the state d_X [ps*D], d_F [ps] that the run had after iteration t_begin - 1
+ * (the output of apo_init_state for t_begin = 1, or of a previous
+ * apo_run_from_state that ended at t_begin - 1).  On return d_X, d_F hold the
+ * state after iteration t_end in its current order (the rank order of
+ * iteration t_end's fitness sort, after the greedy replacement), so that runs
+ * can be split into segments: the segments give the same results, bit for
+ * bit, as one uninterrupted run.  Outputs (device, each may be NULL):
+ * d_best_x [D], d_best_f [1] (the best after t_end) and d_curve
+ * [t_end - t_begin + 2] with d_curve[j] = best fitness after iteration
+ * t_begin - 1 + j.  Stream-ordered. */
+apo_status apo_run_from_state(const apo_problem* prob, const apo_params* params, int t_begin, int t_end,
+                              void* stream, float* d_X, void* d_F, float* d_best_x, double* d_best_f,
+                              float* d_curve);
 
 /* Test hook: iteration `iter` (1..max_iter) of Algorithm 1 applied to a given
  * state.  d_X [ps*D] and d_F [ps] hold the population in its current order;

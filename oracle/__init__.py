@@ -54,7 +54,7 @@ class Problem(C.Structure):
 class Params(C.Structure):
     _fields_ = [("ps", C.c_int), ("np", C.c_int), ("pf_max", C.c_double),
                 ("max_iter", C.c_int), ("seed", C.c_uint32), ("run", C.c_uint32),
-                ("pdr_form", C.c_int)]
+                ("pdr_form", C.c_int), ("pair_policy", C.c_int), ("max_fes", C.c_longlong)]
 
 
 class StepInfo(C.Structure):
@@ -84,6 +84,9 @@ def lib():
         L.orc_candidates.restype = C.c_int
         L.orc_apo_run.argtypes = [P(Problem), P(Params), P(C.c_double), P(C.c_double),
                                   P(C.c_double)]
+        L.orc_apo_run.restype = C.c_int
+        L.orc_iterations.argtypes = [P(Params)]
+        L.orc_iterations.restype = C.c_int
         L.orc_apo_run_many.argtypes = [P(P(Problem)), P(Params), C.c_int, C.c_int, C.c_int,
                                        P(C.c_double), P(C.c_double)]
         L.orc_clamp_eval_select.argtypes = [P(Problem), C.c_int, P(C.c_double), P(C.c_double),
@@ -135,9 +138,14 @@ class OracleProblem:
                    None if spec.hist is None else np.asarray(spec.hist, np.int64))
 
 
-def params(ps, np_=1, pf_max=0.1, max_iter=1000, seed=0, run=0, pdr_form=0):
+def params(ps, np_=1, pf_max=0.1, max_iter=1000, seed=0, run=0, pdr_form=0, pair_policy=0, max_fes=0):
     return Params(int(ps), int(np_), float(pf_max), int(max_iter), int(seed) & 0xFFFFFFFF,
-                  int(run) & 0xFFFFFFFF, int(pdr_form))
+                  int(run) & 0xFFFFFFFF, int(pdr_form), int(pair_policy), int(max_fes))
+
+
+def iterations(prm: Params) -> int:
+    """Iterations a run takes (max_iter, or what the evaluation budget allows)."""
+    return int(lib().orc_iterations(C.byref(prm)))
 
 
 def philox(ctr, key):
@@ -209,9 +217,14 @@ def candidates(prob: OracleProblem, prm: Params, t, k, X, F):
 def apo_run(prob: OracleProblem, prm: Params, want_curve=True):
     best_x = np.empty(prob.D, np.float64)
     best_f = C.c_double()
-    curve = np.empty(prm.max_iter + 1, np.float64) if want_curve else None
-    lib().orc_apo_run(C.byref(prob.c), C.byref(prm), _ptr(best_x, C.c_double), C.byref(best_f),
-                      _ptr(curve, C.c_double))
+    T = iterations(prm)
+    if T < 1:
+        raise ValueError("the evaluation budget allows no iteration")
+    curve = np.empty(T + 1, np.float64) if want_curve else None
+    rc = lib().orc_apo_run(C.byref(prob.c), C.byref(prm), _ptr(best_x, C.c_double), C.byref(best_f),
+                           _ptr(curve, C.c_double))
+    if rc != 0:
+        raise ValueError("orc_apo_run rejected its arguments")
     return best_x, best_f.value, curve
 
 

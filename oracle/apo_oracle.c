@@ -37,6 +37,10 @@
  *       13.53 -> 10).
  *   R12 Otsu thresholds are floor() of the position rounded to binary32 (the
  *       precision the GPU state is stored in), clamped to 0..255, sorted.
+ *   R23 with an evaluation budget MaxFEs counted in objective evaluations
+ *       (the original APO's reading of MaxFEs), the run takes the whole
+ *       iterations that fit: ps evaluations at initialisation, ps per
+ *       iteration; their number is iter_max.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11), key = (seed, run), counter =
@@ -160,6 +164,8 @@ typedef struct {
     uint32_t seed;
     uint32_t run;
     int pdr_form;
+    int pair_policy;   /* reading R2 (0) or its alternative (1), see orc_candidate */
+    long long max_fes; /* > 0: evaluation budget (orc_apo_run), reading R23  */
 } orc_params;
 
 /* Diagnostics of one iteration, all in rank order of that iteration's sort.
@@ -511,8 +517,16 @@ static int orc_candidate(const orc_problem* P, const orc_params* prm, int t, int
                 uint32_t pr[4];
                 orc_draw(seed, run, (uint32_t)t, (uint32_t)r, (uint32_t)(k - 1),
                          ORC_SLOT_PAIR | slot_off, pr);
-                km[k - 1] = (int)orc_IDX(pr[0], (uint32_t)ps);
-                kp[k - 1] = (int)orc_IDX(pr[1], (uint32_t)ps);
+                if (prm->pair_policy == 0) {
+                    /* R2: k-, k+ independent uniform ranks over 1..ps */
+                    km[k - 1] = (int)orc_IDX(pr[0], (uint32_t)ps);
+                    kp[k - 1] = (int)orc_IDX(pr[1], (uint32_t)ps);
+                } else {
+                    /* R2 alternative: k- uniform over the ranks 1..i (at
+                     * least as good as X_i), k+ uniform over i..ps */
+                    km[k - 1] = (int)orc_IDX(pr[0], (uint32_t)i);
+                    kp[k - 1] = r + (int)orc_IDX(pr[1], (uint32_t)(ps - r));
+                }
                 /* Eq. 7 */
                 wa[k - 1] = exp(-fabs(Fs[km[k - 1]] / (Fs[kp[k - 1]] + eps)));
             }
@@ -694,9 +708,30 @@ static int orc_best_index(const double* F, int ps)
 /* A whole run: initialisation, max_iter iterations, the best position and
  * fitness, and the convergence curve curve[t] = best fitness after
  * iteration t (curve[0] after initialisation).  curve may be NULL. */
-int orc_apo_run(const orc_problem* P, const orc_params* prm, double* best_x,
+/* The number of iterations a run takes: max_iter, or, with an evaluation
+ * budget max_fes > 0 (reading R23: MaxFEs counted in objective evaluations,
+ * FEs = ps after the initialisation and += ps per iteration, the loop running
+ * while another whole iteration fits), the largest T with ps (T + 1) <=
+ * max_fes.  That T is iter_max of Eq. 4, 9 and 12.  -1 when nothing fits. */
+int orc_iterations(const orc_params* prm)
+{
+    if (prm->max_fes <= 0) return prm->max_iter;
+    long long fes = prm->ps;   /* the initialisation */
+    int T = 0;
+    while (fes + prm->ps <= prm->max_fes) {
+        fes += prm->ps;
+        ++T;
+    }
+    return T >= 1 ? T : -1;
+}
+
+int orc_apo_run(const orc_problem* P, const orc_params* prm_in, double* best_x,
                 double* best_f, double* curve)
 {
+    orc_params prm_v = *prm_in;
+    const orc_params* prm = &prm_v;
+    prm_v.max_iter = orc_iterations(prm_in);
+    if (prm_v.max_iter < 1) return -1;
     const int ps = prm->ps, D = P->D;
     double* X = (double*)malloc(sizeof(double) * (size_t)ps * D);
     double* F = (double*)malloc(sizeof(double) * (size_t)ps);

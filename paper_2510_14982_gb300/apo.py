@@ -30,6 +30,7 @@ EXPORTS = ("apo_problem_create", "apo_problem_destroy", "apo_problem_dim", "apo_
            "apo_run_device_noalloc",
            "apo_run_batch", "apo_batch_create", "apo_batch_launch", "apo_batch_autotune", "apo_batch_destroy",
            "apo_step", "apo_evaluate", "apo_clamp_eval_select", "apo_histogram_u8",
+           "apo_effective_iterations", "apo_init_state", "apo_run_from_state",
            "apo_mlp_create", "apo_mlp_destroy", "apo_mlp_set_params", "apo_mlp_get_params", "apo_mlp_forward",
            "apo_mlp_gradients", "apo_mlp_train",
            "apo_run_surrogate", "apo_surrogate_candidates", "apo_barrier_selftest",
@@ -45,7 +46,8 @@ class apo_objective_desc(C.Structure):
 
 class apo_params(C.Structure):
     _fields_ = [("ps", C.c_int), ("np", C.c_int), ("pf_max", C.c_double), ("max_iter", C.c_int),
-                ("seed", C.c_uint32), ("run", C.c_uint32), ("pdr_form", C.c_int)]
+                ("seed", C.c_uint32), ("run", C.c_uint32), ("pdr_form", C.c_int), ("pair_policy", C.c_int),
+                ("max_fes", C.c_longlong)]
 
 
 class apo_batch_options(C.Structure):
@@ -84,6 +86,12 @@ _lib.apo_batch_autotune.argtypes = [_P, _P, C.c_int, C.POINTER(apo_batch_options
 _lib.apo_batch_destroy.argtypes = [_P]
 _lib.apo_batch_destroy.restype = None
 _lib.apo_step.argtypes = [_P, C.POINTER(apo_params), C.c_int, _P, _P, _P]
+_lib.apo_effective_iterations.argtypes = [C.POINTER(apo_params)]
+_lib.apo_effective_iterations.restype = C.c_int
+_lib.apo_init_state.argtypes = [_P, C.POINTER(apo_params), _P, _P, _P]
+_lib.apo_init_state.restype = C.c_int
+_lib.apo_run_from_state.argtypes = [_P, C.POINTER(apo_params), C.c_int, C.c_int, _P, _P, _P, _P, _P, _P]
+_lib.apo_run_from_state.restype = C.c_int
 _lib.apo_evaluate.argtypes = [_P, _P, _P, C.c_int, _P]
 _lib.apo_clamp_eval_select.argtypes = [_P, _P, C.c_int, _P, _P, _P, _P]
 _lib.apo_histogram_u8.argtypes = [_P, C.c_int64, C.c_int, _P, _P]
@@ -157,9 +165,15 @@ def apo_last_error() -> str:
     return _lib.apo_last_error().decode()
 
 
-def apo_params_make(ps, np_=1, pf_max=0.1, max_iter=1000, seed=0, run=0, pdr_form=0) -> apo_params:
+def apo_params_make(ps, np_=1, pf_max=0.1, max_iter=1000, seed=0, run=0, pdr_form=0, pair_policy=0,
+                    max_fes=0) -> apo_params:
     return apo_params(int(ps), int(np_), float(pf_max), int(max_iter), int(seed) & 0xFFFFFFFF,
-                      int(run) & 0xFFFFFFFF, int(pdr_form))
+                      int(run) & 0xFFFFFFFF, int(pdr_form), int(pair_policy), int(max_fes))
+
+
+def apo_effective_iterations(params: apo_params) -> int:
+    """Iterations a run with these params takes (max_iter, or what max_fes allows); -1 if invalid."""
+    return int(_lib.apo_effective_iterations(C.byref(params)))
 
 
 class Problem:
@@ -227,7 +241,8 @@ def apo_run(prob: Problem, params: apo_params, stream=None, want_curve=True):
     """apo_run (host outputs, synchronous): returns (best_x, best_f, curve)."""
     best_x = np.empty(prob.D, np.float32)
     best_f = C.c_double()
-    curve = np.empty(params.max_iter + 1, np.float32) if want_curve else None
+    T = apo_effective_iterations(params)
+    curve = np.empty(max(T, 0) + 1, np.float32) if want_curve else None
     _check(_lib.apo_run(prob.handle, C.byref(params), _stream(stream), _np_ptr(best_x, C.c_float),
                         C.byref(best_f), _np_ptr(curve, C.c_float)), "apo_run")
     return best_x, best_f.value, curve
@@ -289,6 +304,20 @@ def apo_batch_create(probs, params, d_best_x, x_stride, d_best_f, d_curves=None,
 def apo_step(prob: Problem, params: apo_params, it: int, d_X, d_F, stream=None):
     _check(_lib.apo_step(prob.handle, C.byref(params), int(it), _stream(stream), _dptr(d_X), _dptr(d_F)),
            "apo_step")
+
+
+def apo_init_state(prob: Problem, params: apo_params, d_X, d_F, stream=None):
+    """apo_init_state: the run's initial population into d_X [ps, D], d_F [ps] (protozoon order)."""
+    _check(_lib.apo_init_state(prob.handle, C.byref(params), _stream(stream), _dptr(d_X), _dptr(d_F)),
+           "apo_init_state")
+
+
+def apo_run_from_state(prob: Problem, params: apo_params, t_begin: int, t_end: int, d_X, d_F, d_best_x=None,
+                       d_best_f=None, d_curve=None, stream=None):
+    """apo_run_from_state: iterations t_begin..t_end from the state (d_X, d_F), which is updated in place."""
+    _check(_lib.apo_run_from_state(prob.handle, C.byref(params), int(t_begin), int(t_end), _stream(stream),
+                                   _dptr(d_X), _dptr(d_F), _dptr(d_best_x), _dptr(d_best_f), _dptr(d_curve)),
+           "apo_run_from_state")
 
 
 def apo_evaluate(prob: Problem, d_X, d_F, stream=None):
@@ -376,7 +405,7 @@ def apo_run_surrogate(prob: Problem, params: apo_params, sp: apo_surrogate_param
     """apo_run_surrogate (host outputs, synchronous): (best_x, best_f, curve, stats dict)."""
     best_x = np.empty(prob.D, np.float32)
     best_f = C.c_double()
-    curve = np.empty(params.max_iter + 1, np.float32) if want_curve else None
+    curve = np.empty(max(apo_effective_iterations(params), 0) + 1, np.float32) if want_curve else None
     st = apo_surrogate_stats()
     _check(_lib.apo_run_surrogate(prob.handle, C.byref(params), C.byref(sp), _stream(stream),
                                   _np_ptr(best_x, C.c_float), C.byref(best_f), _np_ptr(curve, C.c_float),

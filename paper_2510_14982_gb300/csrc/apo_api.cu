@@ -435,11 +435,7 @@ apo_status get_thr_dr(int ps, int form, int dev, const uint32_t** out)
     auto it = c.dr.find(key);
     if (it != c.dr.end()) { *out = it->second; return APO_OK; }
     std::vector<uint32_t> thr(ps);
-    for (int i = 1; i <= ps; ++i) {
-        const double cv = cos((1.0 - (double)i / (double)ps) * M_PI);
-        const double p = form == 0 ? 0.5 * (1.0 - cv) : 0.5 * (1.0 + cv);
-        thr[i - 1] = (uint32_t)ceil(p * 16777216.0);
-    }
+    fill_sched_tables(ps, form, 0, thr.data(), nullptr, nullptr, nullptr);
     uint32_t* d = nullptr;
     APO_CUDA(cudaMalloc(&d, sizeof(uint32_t) * ps));
     APO_CUDA(cudaMemcpy(d, thr.data(), sizeof(uint32_t) * ps, cudaMemcpyHostToDevice));
@@ -462,13 +458,7 @@ apo_status get_sched(int T, int dev, const uint32_t** thr_ah, const float** fsc,
     } else {
         std::vector<uint32_t> a(T + 1);
         std::vector<float> f(T + 1), n(T + 1);
-        for (int t = 0; t <= T; ++t) {
-            const double cv = cos(((double)t / (double)T) * M_PI);
-            const double pah = 0.5 * (1.0 + cv);
-            a[t] = (uint32_t)ceil(pah * 16777216.0);
-            f[t] = (float)(1.0 + cv);
-            n[t] = (float)(1.0 - (double)t / (double)T);
-        }
+        fill_sched_tables(0, 0, T, nullptr, a.data(), f.data(), n.data());
         const size_t stride = align_up((size_t)(T + 1) * 4, 256);
         APO_CUDA(cudaMalloc(&d, 3 * stride));
         unsigned char* b = static_cast<unsigned char*>(d);
@@ -501,15 +491,13 @@ int* device_status(int dev)
     return p;
 }
 
-apo_status check_params(const apo_problem* P, const apo_params* p)
+// Validates a problem and its params (normalize_params) and writes the
+// resolved params (max_fes turned into max_iter) to *q.
+apo_status check_params(const apo_problem* P, const apo_params* p, apo_params* q)
 {
     if (!P || !p) { set_err("problem and params must not be NULL"); return APO_ERR_INVALID_ARG; }
-    if (p->ps < 2) { set_err("ps must be >= 2"); return APO_ERR_INVALID_ARG; }
-    if (p->np < 1 || 2 * p->np >= p->ps) { set_err("np must satisfy 1 <= np and 2 np < ps"); return APO_ERR_INVALID_ARG; }
-    if (!(p->pf_max >= 0.0 && p->pf_max <= 1.0)) { set_err("pf_max must be in [0, 1]"); return APO_ERR_INVALID_ARG; }
-    if (p->max_iter < 1) { set_err("max_iter must be >= 1"); return APO_ERR_INVALID_ARG; }
-    if (p->pdr_form != 0 && p->pdr_form != 1) { set_err("pdr_form must be 0 or 1"); return APO_ERR_INVALID_ARG; }
-    if (p->ps > (1 << 20)) { set_err("ps above 2^20 is not supported"); return APO_ERR_UNSUPPORTED; }
+    if (const char* why = normalize_params(p, q)) { set_err("%s", why); return APO_ERR_INVALID_ARG; }
+    if (q->ps > (1 << 20)) { set_err("ps above 2^20 is not supported"); return APO_ERR_UNSUPPORTED; }
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != P->device) { set_err("problem belongs to device %d, current device is %d", P->device, dev); return APO_ERR_INVALID_ARG; }
@@ -653,7 +641,8 @@ apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, b
         const size_t fsz = s.P->kind == APO_OBJ_OTSU ? 8 : 4;
         const int W = (ps + 31) / 32;
         off_dr[i] = take(sizeof(uint32_t) * W * (size_t)(s.t_end + 1));
-        const bool need_global = !plans[k].resident || (s.flags & kFlagStepOut);
+        // a run that starts from a given state reads it from global memory
+        const bool need_global = !plans[k].resident || !(s.flags & kFlagInit);
         off_x0[i] = need_global ? take((size_t)ps * Dp * 4) : 0;
         off_x1[i] = need_global ? take((size_t)ps * Dp * 4) : 0;
         off_f0[i] = need_global ? take(ps * fsz) : 0;
@@ -689,6 +678,7 @@ apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, b
         R.prob = s.P->dev;
         R.plan = plans[k];
         R.ps = s.prm.ps; R.np = s.prm.np; R.T = s.prm.max_iter; R.pdr_form = s.prm.pdr_form;
+        R.pair_policy = s.prm.pair_policy;
         R.pf_max = s.prm.pf_max; R.seed = s.prm.seed; R.run = s.prm.run;
         R.t_begin = s.t_begin; R.t_end = s.t_end; R.flags = s.flags;
         R.g = g_of[i];
@@ -748,7 +738,7 @@ apo_status launch_prepared(const Prepared& PR, cudaStream_t st)
     APO_CUDA(cudaMemsetAsync(PR.d_bars, 0, kBarStride * (size_t)PR.n, st));
     for (int i = 0; i < PR.n; ++i) {
         const RunSpec& s = PR.order[i];
-        if (!(s.flags & kFlagStepOut)) continue;
+        if ((s.flags & kFlagInit) || !s.X_in) continue;   // runs from a given state: copy it in
         const size_t fsz = s.P->kind == APO_OBJ_OTSU ? 8 : 4;
         APO_CUDA(cudaMemcpy2DAsync(base + PR.x0_off[i], (size_t)s.P->Dp * 4, s.X_in, (size_t)s.P->D * 4,
                                    (size_t)s.P->D * 4, s.prm.ps, cudaMemcpyDeviceToDevice, st));
@@ -756,7 +746,7 @@ apo_status launch_prepared(const Prepared& PR, cudaStream_t st)
     }
     cudaError_t e = launch_dr(PR.d_runs, PR.d_offs, PR.n, PR.n_work, PR.max_ps_pad, st);
     if (e != cudaSuccess) { set_err("Dr selection launch failed: %s", cudaGetErrorString(e)); return APO_ERR_CUDA; }
-    const bool timed = g_ev_before && g_ev_after && !(PR.order[0].flags & kFlagStepOut);
+    const bool timed = g_ev_before && g_ev_after && !(PR.order[0].flags & (kFlagStepOut | kFlagStateOut));
     if (timed) APO_CUDA(cudaEventRecord(g_ev_before, st));
     for (size_t l = 0; l < PR.launches.size() && e == cudaSuccess; ++l) {
         const LaunchInfo& L = PR.launches[l];
@@ -808,12 +798,13 @@ apo_status read_device_status(int dev)
 extern "C" apo_status apo_run_device(const apo_problem* P, const apo_params* p, void* stream, float* d_best_x,
                                      double* d_best_f, float* d_curve)
 {
-    apo_status rc = check_params(P, p);
+    apo_params q;
+    apo_status rc = check_params(P, p, &q);
     if (rc != APO_OK) return rc;
     if (!d_best_x || !d_best_f) { set_err("d_best_x and d_best_f must not be NULL"); return APO_ERR_INVALID_ARG; }
     std::vector<RunSpec> specs(1);
     RunSpec& s = specs[0];
-    s.P = P; s.prm = *p; s.t_begin = 1; s.t_end = p->max_iter; s.flags = kFlagInit;
+    s.P = P; s.prm = q; s.t_begin = 1; s.t_end = q.max_iter; s.flags = kFlagInit;
     s.best_x = d_best_x; s.best_f = d_best_f; s.curve = d_curve; s.X_in = nullptr; s.F_in = nullptr;
     return launch_runs(specs, static_cast<cudaStream_t>(stream));
 }
@@ -821,11 +812,12 @@ extern "C" apo_status apo_run_device(const apo_problem* P, const apo_params* p, 
 extern "C" apo_status apo_run(const apo_problem* P, const apo_params* p, void* stream, float* best_x,
                               double* best_f, float* curve)
 {
-    apo_status rc = check_params(P, p);
+    apo_params q;
+    apo_status rc = check_params(P, p, &q);
     if (rc != APO_OK) return rc;
     if (!best_x || !best_f) { set_err("best_x and best_f must not be NULL"); return APO_ERR_INVALID_ARG; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t bx = align_up((size_t)P->D * 4, 256), bc = (size_t)(p->max_iter + 1) * 4;
+    const size_t bx = align_up((size_t)P->D * 4, 256), bc = (size_t)(q.max_iter + 1) * 4;
     void* out = nullptr;
     APO_CUDA(cudaMallocAsync(&out, bx + 256 + bc, st));
     unsigned char* b = static_cast<unsigned char*>(out);
@@ -857,14 +849,15 @@ extern "C" apo_status apo_run_batch(const apo_problem* const* probs, const apo_p
     }
     std::vector<RunSpec> specs(n_runs);
     for (int k = 0; k < n_runs; ++k) {
-        apo_status rc = check_params(probs[k], &params[k]);
+        apo_params q;
+        apo_status rc = check_params(probs[k], &params[k], &q);
         if (rc != APO_OK) return rc;
-        if (x_stride < probs[k]->D || (d_curves && curve_stride < params[k].max_iter + 1)) {
+        if (x_stride < probs[k]->D || (d_curves && curve_stride < q.max_iter + 1)) {
             set_err("x_stride / curve_stride too small for run %d", k);
             return APO_ERR_INVALID_ARG;
         }
         RunSpec& s = specs[k];
-        s.P = probs[k]; s.prm = params[k]; s.t_begin = 1; s.t_end = params[k].max_iter; s.flags = kFlagInit;
+        s.P = probs[k]; s.prm = q; s.t_begin = 1; s.t_end = q.max_iter; s.flags = kFlagInit;
         s.best_x = d_best_x + (size_t)k * x_stride;
         s.best_f = d_best_f + k;
         s.curve = d_curves ? d_curves + (size_t)k * curve_stride : nullptr;
@@ -891,14 +884,15 @@ apo_status batch_specs(const apo_problem* const* probs, const apo_params* params
     }
     specs.resize(n_runs);
     for (int k = 0; k < n_runs; ++k) {
-        apo_status rc = check_params(probs[k], &params[k]);
+        apo_params q;
+        apo_status rc = check_params(probs[k], &params[k], &q);
         if (rc != APO_OK) return rc;
-        if (x_stride < probs[k]->D || (d_curves && curve_stride < params[k].max_iter + 1)) {
+        if (x_stride < probs[k]->D || (d_curves && curve_stride < q.max_iter + 1)) {
             set_err("x_stride / curve_stride too small for run %d", k);
             return APO_ERR_INVALID_ARG;
         }
         RunSpec& s = specs[k];
-        s.P = probs[k]; s.prm = params[k]; s.t_begin = 1; s.t_end = params[k].max_iter; s.flags = kFlagInit;
+        s.P = probs[k]; s.prm = q; s.t_begin = 1; s.t_end = q.max_iter; s.flags = kFlagInit;
         s.best_x = d_best_x + (size_t)k * x_stride;
         s.best_f = d_best_f + k;
         s.curve = d_curves ? d_curves + (size_t)k * curve_stride : nullptr;
@@ -994,14 +988,60 @@ extern "C" apo_status apo_batch_autotune(apo_batch* B, void* stream, int probe_i
 extern "C" apo_status apo_step(const apo_problem* P, const apo_params* p, int iter, void* stream, float* d_X,
                                void* d_F)
 {
-    apo_status rc = check_params(P, p);
+    apo_params q;
+    apo_status rc = check_params(P, p, &q);
     if (rc != APO_OK) return rc;
-    if (iter < 1 || iter > p->max_iter) { set_err("iter must be in 1..max_iter"); return APO_ERR_INVALID_ARG; }
+    if (iter < 1 || iter > q.max_iter) { set_err("iter must be in 1..max_iter"); return APO_ERR_INVALID_ARG; }
     if (!d_X || !d_F) { set_err("d_X and d_F must not be NULL"); return APO_ERR_INVALID_ARG; }
     std::vector<RunSpec> specs(1);
     RunSpec& s = specs[0];
-    s.P = P; s.prm = *p; s.t_begin = iter; s.t_end = iter; s.flags = kFlagStepOut;
+    s.P = P; s.prm = q; s.t_begin = iter; s.t_end = iter; s.flags = kFlagStepOut;
     s.best_x = nullptr; s.best_f = nullptr; s.curve = nullptr; s.X_in = d_X; s.F_in = d_F;
+    return launch_runs(specs, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int apo_effective_iterations(const apo_params* p)
+{
+    apo_params q;
+    if (normalize_params(p, &q)) return -1;
+    return q.max_iter;
+}
+
+extern "C" apo_status apo_init_state(const apo_problem* P, const apo_params* p, void* stream, float* d_X, void* d_F)
+{
+    apo_params q;
+    apo_status rc = check_params(P, p, &q);
+    if (rc != APO_OK) return rc;
+    if (!d_X || !d_F) { set_err("d_X and d_F must not be NULL"); return APO_ERR_INVALID_ARG; }
+    std::vector<RunSpec> specs(1);
+    RunSpec& s = specs[0];
+    // no iteration: initialisation, then the state in protozoon order
+    s.P = P; s.prm = q; s.t_begin = 1; s.t_end = 0; s.flags = kFlagInit | kFlagStateOut;
+    s.best_x = nullptr; s.best_f = nullptr; s.curve = nullptr; s.X_in = d_X; s.F_in = d_F;
+    return launch_runs(specs, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" apo_status apo_run_from_state(const apo_problem* P, const apo_params* p, int t_begin, int t_end,
+                                         void* stream, float* d_X, void* d_F, float* d_best_x, double* d_best_f,
+                                         float* d_curve)
+{
+    apo_params q;
+    apo_status rc = check_params(P, p, &q);
+    if (rc != APO_OK) return rc;
+    if (t_begin < 1 || t_end < t_begin - 1 || t_end > q.max_iter) {
+        set_err("need 1 <= t_begin and t_begin - 1 <= t_end <= T (T = %d)", q.max_iter);
+        return APO_ERR_INVALID_ARG;
+    }
+    if (!d_X || !d_F) { set_err("d_X and d_F must not be NULL"); return APO_ERR_INVALID_ARG; }
+    std::vector<RunSpec> specs(1);
+    RunSpec& s = specs[0];
+    s.P = P; s.prm = q; s.t_begin = t_begin; s.t_end = t_end; s.flags = kFlagStateOut;
+    // the kernels write curve[t - 1] for t = t_begin .. t_end + 1: index the
+    // caller's array from iteration t_begin - 1
+    s.curve = d_curve ? reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(d_curve) -
+                                                 sizeof(float) * (size_t)(t_begin - 1))
+                      : nullptr;
+    s.best_x = d_best_x; s.best_f = d_best_f; s.X_in = d_X; s.F_in = d_F;
     return launch_runs(specs, static_cast<cudaStream_t>(stream));
 }
 

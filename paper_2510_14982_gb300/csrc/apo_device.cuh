@@ -41,7 +41,8 @@ enum Kind : int { kSphere = 0, kElliptic = 1, kRosenbrock = 2, kRastrigin = 3, k
 
 // Run flags.
 constexpr int kFlagInit = 1;      // initialise the population (t = 0)
-constexpr int kFlagStepOut = 2;   // write the rank-ordered state to X_out / F_out
+constexpr int kFlagStepOut = 2;   // write the rank-ordered state to X_out / F_out (no best, no curve)
+constexpr int kFlagStateOut = 4;  // also write the state after t_end (current order) to X_out / F_out
 
 // One shifted-rotated component: z = M (x - o), then a segmented form:
 // [0, s1) elliptic with weights ew, [s1, s2) Rosenbrock chain, [s2, D) Rastrigin.
@@ -135,6 +136,8 @@ struct ApoRun {
     DevProblem prob;
     SmemPlan plan;
     int ps, np, T, pdr_form;
+    int pair_policy;     // 0: k-, k+ uniform over all ranks; 1: k- in [0, r], k+ in [r, ps)
+    int pad_;
     double pf_max;
     uint32_t seed, run;
     int t_begin, t_end;  // iterations executed by this launch

@@ -255,7 +255,9 @@ __device__ __forceinline__ void run_one(const ApoRun& R, int local, unsigned cha
     }
 
     const uint32_t* perm = S.perm[pc];
-    if (R.flags & kFlagStepOut) {
+    if (R.flags & (kFlagStepOut | kFlagStateOut)) {
+        // the state in its current order: the rank order of the last
+        // iteration's sort (protozoon order when no iteration ran)
         float* xo = R.X_out;
         FitT* fo = static_cast<FitT*>(R.F_out);
         for (int r = r0 + warp; r < r1; r += nw) {
@@ -263,7 +265,8 @@ __device__ __forceinline__ void run_one(const ApoRun& R, int local, unsigned cha
             for (int d = lane; d < D; d += 32) xo[(size_t)r * D + d] = ldst(Xs[cur] + (size_t)slot * Dp + d, res);
             if (lane == 0) fo[r] = ldst(Fs[cur] + slot, res);
         }
-    } else if (local == 0) {
+    }
+    if (!(R.flags & kFlagStepOut) && local == 0) {
         find_best<FitT>(S, Fs[cur], perm, ps, res, static_cast<KT*>(S.red), s_int);
         const int slot = (int)perm[*s_int];
         const FitT fb = ldst(Fs[cur] + slot, res);
@@ -510,7 +513,19 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
     int cur = 0;
     bool keys_ready = false;   // the greedy step already wrote the own keys
     const bool step_out = (R.flags & kFlagStepOut) != 0;
+    // the state after t_end is written out (apo_step: and the launch ends there)
+    const bool state_out = step_out || (R.flags & kFlagStateOut) != 0;
     uint8_t* nloc = S.nloc;    // [nown]: buffer bit of each own slot after the greedy step
+    if (state_out && R.t_end < R.t_begin) {
+        // no iteration: the state as initialised or given, in slot order
+        float* xo = R.X_out;
+        FitT* fo = static_cast<FitT*>(R.F_out);
+        for (int m = warp; m < nown; m += nw) {
+            const int r = pos_of(m);
+            for (int d = lane; d < D; d += 32) xo[(size_t)r * D + d] = ldst(Xs[0] + (size_t)r * Dp + d, false);
+            if (lane == 0) fo[r] = ldst(Fs[0] + r, false);
+        }
+    }
     for (int t = R.t_begin;; ++t) {
         // R1: own keys (F, rank in the current order), sorted and published
         if (!keys_ready)
@@ -628,7 +643,7 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
             // A's arrival (below), so that its release need not wait for them
             // to drain; nothing reads them before barrier B.  The step output
             // reads them in this iteration, so it takes them here.
-            const bool hold = c0 + CH >= nown && !(step_out && t == R.t_end);
+            const bool hold = c0 + CH >= nown && !(state_out && t == R.t_end);
             for (int row = tid; row < rows; row += NT) {
                 const uint32_t e = perm[pos_of(c0 + row)];
                 const uint32_t loc = e >> 31;
@@ -650,7 +665,7 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
         if (curve_w) R.curve[t - 1] = (float)curve_v;
         keys_ready = true;
         cur ^= 1;
-        if (step_out && t == R.t_end) {
+        if (state_out && t == R.t_end) {
             float* xo = R.X_out;
             FitT* fo = static_cast<FitT*>(R.F_out);
             for (int m = warp; m < nown; m += nw) {
@@ -660,7 +675,7 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
                 for (int d = lane; d < D; d += 32) xo[(size_t)r * D + d] = ldst(src + d, false);
                 if (lane == 0) fo[r] = ldst(Fs[cur] + slot, false);
             }
-            break;
+            if (step_out) break;   // apo_step: no best, no curve
         }
     }
     __syncthreads();

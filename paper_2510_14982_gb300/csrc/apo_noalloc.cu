@@ -7,14 +7,15 @@
 //
 // Instead of a per-call workspace, every call uses one file-scope device
 // array of kScratchBytes (8 MiB).  Each device that loads the library holds
-// that array until the process exits.  Its device address is looked up once
-// per device, on the first call made with that device current; that first
-// call should therefore come before any stream capture.  Every call reuses
-// the same array, which keeps the previous call's contents: the words that
-// must start at zero (status, work-queue counter, barrier words) are cleared
-// by every call, and two calls whose work overlaps on the GPU (from two host
-// threads, or on two streams) race on the array.  The call returns after its
-// run has finished, so calls from one host thread never overlap.
+// that array until the process exits.  Its device address is looked up with
+// cudaGetSymbolAddress on the first call made with a device (and context)
+// current and cached for that context; a call after cudaDeviceReset, which
+// brings a new context, looks it up again.  That first call should come
+// before any stream capture.  Every call reuses the same array, which keeps
+// the previous call's contents: the words that must start at zero (status,
+// work-queue counter, barrier words) are cleared by every call, and two calls
+// whose work overlaps on the GPU (from two host threads, or on two streams)
+// race on the array.  The call returns after its run has finished.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -34,19 +35,37 @@ static __device__ __align__(256) unsigned char apo_noalloc_scratch[8u << 20];
 namespace {
 
 constexpr size_t kScratchBytes = 8u << 20;
-constexpr size_t kSmemMaxNA = 232448 - 2048;
 constexpr int kQueueMaxPsNA = 1024;
 constexpr int kGridMinRowsNA = 8;
 constexpr int kMaxDevices = 64;
 
 std::mutex g_na_mu;
 void* g_na_addr[kMaxDevices] = {};
+void* g_na_ctx[kMaxDevices] = {};   // the context the cached address belongs to
 
 thread_local char g_na_err[256] = "";
 
 size_t al(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Device address of the scratch array on the current device (looked up once).
+// The current driver context (nullptr when the driver entry point is not
+// available), so that a cached address is never used in a later context.
+void* current_context()
+{
+    using Fn = int (*)(void**);
+    static Fn fn = []() -> Fn {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<Fn>(f);
+    }();
+    void* ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
+
+// Device address of the scratch array on the current device and context.
 apo_status scratch_address(int dev, unsigned char** out)
 {
     if (dev < 0 || dev >= kMaxDevices) {
@@ -54,7 +73,8 @@ apo_status scratch_address(int dev, unsigned char** out)
         return APO_ERR_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_addr[dev]) {
+    void* ctx = current_context();
+    if (!g_na_addr[dev] || !ctx || ctx != g_na_ctx[dev]) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, apo_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -63,6 +83,7 @@ apo_status scratch_address(int dev, unsigned char** out)
             return APO_ERR_CUDA;
         }
         g_na_addr[dev] = p;
+        g_na_ctx[dev] = ctx;
     }
     *out = static_cast<unsigned char*>(g_na_addr[dev]);
     return APO_OK;
@@ -70,21 +91,25 @@ apo_status scratch_address(int dev, unsigned char** out)
 
 }  // namespace
 
-extern "C" apo_status apo_run_device_noalloc(const apo_problem* P, const apo_params* p, void* stream,
+extern "C" apo_status apo_run_device_noalloc(const apo_problem* P, const apo_params* p_in, void* stream,
                                              float* d_best_x, double* d_best_f, float* d_curve)
 {
     auto fail = [](apo_status s, const char* msg) {
         apo::set_last_error(msg);
         return s;
     };
-    if (!P || !p || !d_best_x || !d_best_f) return fail(APO_ERR_INVALID_ARG, "NULL problem, params or output");
-    if (p->ps < 2 || p->np < 1 || 2 * p->np >= p->ps || !(p->pf_max >= 0.0 && p->pf_max <= 1.0) ||
-        p->max_iter < 1 || (p->pdr_form != 0 && p->pdr_form != 1))
-        return fail(APO_ERR_INVALID_ARG, "params out of range (ps >= 2, 1 <= np, 2 np < ps, "
-                                         "0 <= pf_max <= 1, max_iter >= 1, pdr_form 0 or 1)");
+    if (!P || !p_in || !d_best_x || !d_best_f) return fail(APO_ERR_INVALID_ARG, "NULL problem, params or output");
+    apo_params q;
+    if (const char* why = normalize_params(p_in, &q)) return fail(APO_ERR_INVALID_ARG, why);
+    const apo_params* p = &q;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device)
         return fail(APO_ERR_INVALID_ARG, "the problem belongs to another device");
+    int smem_optin = 0;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return fail(APO_ERR_CUDA, "cannot read the shared-memory limit");
+    // the kernels keep less than 2 KB of static shared memory beside the plan
+    const size_t kSmemMaxNA = (size_t)smem_optin - 2048;
     unsigned char* base = nullptr;
     apo_status rc = scratch_address(dev, &base);
     if (rc != APO_OK) return fail(rc, g_na_err);
@@ -123,20 +148,10 @@ extern "C" apo_status apo_run_device_noalloc(const apo_problem* P, const apo_par
         return fail(APO_ERR_UNSUPPORTED, msg);
     }
 
-    // schedule tables of Eq. 4, 9, 12 and 13 (the same formulas as apo_run_device)
+    // schedule tables of Eq. 4, 9, 12 and 13 (the same helper as apo_run_device)
     std::vector<uint32_t> thr(ps), ah(T + 1);
     std::vector<float> fs(T + 1), ns(T + 1);
-    for (int i = 1; i <= ps; ++i) {
-        const double cv = cos((1.0 - (double)i / (double)ps) * M_PI);
-        const double pr = p->pdr_form == 0 ? 0.5 * (1.0 - cv) : 0.5 * (1.0 + cv);
-        thr[i - 1] = (uint32_t)ceil(pr * 16777216.0);
-    }
-    for (int t = 0; t <= T; ++t) {
-        const double cv = cos(((double)t / (double)T) * M_PI);
-        ah[t] = (uint32_t)ceil(0.5 * (1.0 + cv) * 16777216.0);
-        fs[t] = (float)(1.0 + cv);
-        ns[t] = (float)(1.0 - (double)t / (double)T);
-    }
+    fill_sched_tables(ps, p->pdr_form, T, thr.data(), ah.data(), fs.data(), ns.data());
 
     int g = 1;
     if (grid) {
@@ -149,6 +164,7 @@ extern "C" apo_status apo_run_device_noalloc(const apo_problem* P, const apo_par
     R.prob = P->dev;
     R.plan = plan;
     R.ps = ps; R.np = p->np; R.T = T; R.pdr_form = p->pdr_form; R.pf_max = p->pf_max;
+    R.pair_policy = p->pair_policy;
     R.seed = p->seed; R.run = p->run; R.t_begin = 1; R.t_end = T; R.flags = kFlagInit; R.g = g;
     R.thr_dr = reinterpret_cast<const uint32_t*>(base + o_thr);
     R.thr_ah = reinterpret_cast<const uint32_t*>(base + o_ah);

@@ -550,7 +550,12 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     const uint32_t ei = perm[r];
     const uint32_t p0 = __shfl_sync(0xffffffffu, jw.x, jb + 2), p1 = __shfl_sync(0xffffffffu, jw.y, jb + 2);
     const uint32_t aj = perm[idx_draw(sc2.y, (uint32_t)ps)];
-    const uint32_t aa = perm[idx_draw(p0, (uint32_t)ps)], ab = perm[idx_draw(p1, (uint32_t)ps)];
+    // the pair ranks of Eq. 6-7: uniform over all ranks (pair policy 0), or
+    // k- among the ranks 0..r and k+ among r..ps-1 (pair policy 1)
+    const bool pol = R.pair_policy != 0;
+    const uint32_t na = pol ? (uint32_t)(r + 1) : (uint32_t)ps, nb = pol ? (uint32_t)(ps - r) : (uint32_t)ps;
+    const uint32_t ob = pol ? (uint32_t)r : 0u;
+    const uint32_t aa = perm[idx_draw(p0, na)], ab = perm[ob + idx_draw(p1, nb)];
     const uint32_t ha = perm[r - 1 < 0 ? 0 : r - 1], hb = perm[r + 1 > ps - 1 ? ps - 1 : r + 1];
     const bool autot = mode == kAutotrophic, het = mode == kHeterotrophic;
     const uint32_t ej = autot ? aj : ei;
@@ -623,8 +628,8 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
                     p0 = pr.x;
                     p1 = pr.y;
                 }
-                ea = perm[idx_draw(p0, (uint32_t)ps)];
-                eb = perm[idx_draw(p1, (uint32_t)ps)];
+                ea = perm[idx_draw(p0, na)];
+                eb = perm[ob + idx_draw(p1, nb)];
             } else {
                 ea = perm[r - k < 0 ? 0 : r - k];
                 eb = perm[r + k > ps - 1 ? ps - 1 : r + k];

@@ -2,6 +2,7 @@
 // launching path so that the layout always matches the device carve().
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstring>
 
@@ -10,6 +11,54 @@
 namespace apo {
 
 inline size_t plan_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Validates the Algorithm 1 inputs of every entry point and resolves the
+// evaluation budget: with max_fes > 0 the run takes T = floor(max_fes / ps)
+// - 1 whole iterations (ps evaluations at initialisation, ps per iteration)
+// and T replaces max_iter, the iter_max of Eq. 4, 9 and 12.  Returns nullptr
+// and writes *out, or returns the reason the params are invalid.
+inline const char* normalize_params(const apo_params* p, apo_params* out)
+{
+    if (!p) return "params must not be NULL";
+    if (p->ps < 2) return "ps must be >= 2";
+    if (p->np < 1 || 2 * p->np >= p->ps) return "np must satisfy 1 <= np and 2 np < ps";
+    if (!(p->pf_max >= 0.0 && p->pf_max <= 1.0)) return "pf_max must be in [0, 1]";
+    if (p->pdr_form != 0 && p->pdr_form != 1) return "pdr_form must be 0 or 1";
+    if (p->pair_policy != 0 && p->pair_policy != 1) return "pair_policy must be 0 or 1";
+    if (p->max_fes < 0) return "max_fes must be >= 0";
+    apo_params q = *p;
+    if (p->max_fes > 0) {
+        const long long T = p->max_fes / p->ps - 1;
+        if (T < 1) return "max_fes must allow one iteration (max_fes >= 2 ps)";
+        if (T > (1 << 30)) return "max_fes allows more than 2^30 iterations";
+        q.max_iter = (int)T;
+    }
+    if (q.max_iter < 1) return "max_iter must be >= 1";
+    *out = q;
+    return nullptr;
+}
+
+// Host images of the schedule tables: Eq. 13 as a 24-bit threshold per rank
+// i = 1..ps (form 0 as printed, form 1 mirrored; rank i goes dormant iff
+// ((r >> 8) + 1) < ceil(p_dr(i) 2^24)), and per t = 0..T the Eq. 12
+// threshold ceil(p_ah(t) 2^24), the Eq. 4 factor 1 + cos(pi t / T) and the
+// Eq. 9 factor 1 - t / T.  Any of the outputs may be nullptr.
+inline void fill_sched_tables(int ps, int pdr_form, int T, uint32_t* thr_dr, uint32_t* thr_ah, float* fsc,
+                              float* nsc)
+{
+    if (thr_dr)
+        for (int i = 1; i <= ps; ++i) {
+            const double cv = cos((1.0 - (double)i / (double)ps) * M_PI);
+            const double pr = pdr_form == 0 ? 0.5 * (1.0 - cv) : 0.5 * (1.0 + cv);
+            thr_dr[i - 1] = (uint32_t)ceil(pr * 16777216.0);
+        }
+    for (int t = 0; t <= T && (thr_ah || fsc || nsc); ++t) {
+        const double cv = cos(((double)t / (double)T) * M_PI);
+        if (thr_ah) thr_ah[t] = (uint32_t)ceil(0.5 * (1.0 + cv) * 16777216.0);
+        if (fsc) fsc[t] = (float)(1.0 + cv);
+        if (nsc) nsc[t] = (float)(1.0 - (double)t / (double)T);
+    }
+}
 inline int plan_pow2(int v)
 {
     int p = 1;

@@ -648,13 +648,15 @@ cudaError_t launch_surr_q(int qpl, int which, dim3 grid, size_t smem, cudaStream
 // Test hook: the k candidates of every protozoon at iteration `iter` from a
 // given population, generated by the surrogate path's own sort and
 // candidate kernels (candidate c draws from the plain slots | (c << 8)).
-extern "C" apo_status apo_surrogate_candidates(const apo_problem* P, const apo_params* p, int iter, int k,
+extern "C" apo_status apo_surrogate_candidates(const apo_problem* P, const apo_params* p_in, int iter, int k,
                                                void* stream, const float* d_X, const float* d_F, float* d_Xcand)
 {
-    if (!P || !p || !d_X || !d_F || !d_Xcand) { apo::set_last_error("apo_surrogate_candidates: NULL argument"); return APO_ERR_INVALID_ARG; }
+    if (!P || !p_in || !d_X || !d_F || !d_Xcand) { apo::set_last_error("apo_surrogate_candidates: NULL argument"); return APO_ERR_INVALID_ARG; }
     if (P->kind == APO_OBJ_OTSU) { apo::set_last_error("apo_surrogate_candidates: float objectives only"); return APO_ERR_UNSUPPORTED; }
-    if (p->ps < 2 || p->np < 1 || 2 * p->np >= p->ps || !(p->pf_max >= 0.0 && p->pf_max <= 1.0) || p->max_iter < 1 ||
-        (p->pdr_form != 0 && p->pdr_form != 1) || iter < 1 || iter > p->max_iter || k < 1 || k > 32) {
+    apo_params q;
+    if (const char* why = normalize_params(p_in, &q)) { apo::set_last_error(why); return APO_ERR_INVALID_ARG; }
+    const apo_params* p = &q;
+    if (iter < 1 || iter > p->max_iter || k < 1 || k > 32) {
         apo::set_last_error("apo_surrogate_candidates: arguments out of range");
         return APO_ERR_INVALID_ARG;
     }
@@ -678,6 +680,7 @@ extern "C" apo_status apo_surrogate_candidates(const apo_problem* P, const apo_p
     R.prob = P->dev;
     R.plan = plan;
     R.ps = ps; R.np = p->np; R.T = T; R.pdr_form = p->pdr_form; R.pf_max = p->pf_max;
+    R.pair_policy = p->pair_policy;
     R.seed = p->seed; R.run = p->run; R.t_begin = iter; R.t_end = iter; R.flags = 0; R.g = 1;
     apo_status rc = sched_tables(ps, p->pdr_form, T, &R.thr_dr, &R.thr_ah, &R.fsc, &R.nsc);
     R.drmask = reinterpret_cast<const uint32_t*>(b + o_dr);
@@ -724,17 +727,15 @@ extern "C" apo_status apo_surrogate_candidates(const apo_problem* P, const apo_p
     return APO_OK;
 }
 
-extern "C" apo_status apo_run_surrogate(const apo_problem* P, const apo_params* p, const apo_surrogate_params* sp,
+extern "C" apo_status apo_run_surrogate(const apo_problem* P, const apo_params* p_in, const apo_surrogate_params* sp,
                                         void* stream, float* best_x, double* best_f, float* curve,
                                         apo_surrogate_stats* stats)
 {
-    if (!P || !p || !sp || !best_x || !best_f) { apo::set_last_error("apo_run_surrogate: NULL argument"); return APO_ERR_INVALID_ARG; }
+    if (!P || !p_in || !sp || !best_x || !best_f) { apo::set_last_error("apo_run_surrogate: NULL argument"); return APO_ERR_INVALID_ARG; }
     if (P->kind == APO_OBJ_OTSU) { apo::set_last_error("apo_run_surrogate: float objectives only"); return APO_ERR_UNSUPPORTED; }
-    if (p->ps < 2 || p->np < 1 || 2 * p->np >= p->ps || !(p->pf_max >= 0.0 && p->pf_max <= 1.0) || p->max_iter < 1 ||
-        (p->pdr_form != 0 && p->pdr_form != 1)) {
-        apo::set_last_error("apo_run_surrogate: params out of range");
-        return APO_ERR_INVALID_ARG;
-    }
+    apo_params q;
+    if (const char* why = normalize_params(p_in, &q)) { apo::set_last_error(why); return APO_ERR_INVALID_ARG; }
+    const apo_params* p = &q;
     if (p->ps > 4096) { apo::set_last_error("apo_run_surrogate: ps above 4096"); return APO_ERR_UNSUPPORTED; }
     const int k = sp->k, R_every = sp->retrain_every;
     if (k < 1 || k > 32 || R_every < 1 || sp->archive_cap < p->ps || sp->train_steps < 0 || sp->batch < 1) {
@@ -798,6 +799,7 @@ extern "C" apo_status apo_run_surrogate(const apo_problem* P, const apo_params* 
     R.prob = P->dev;
     R.plan = plan;
     R.ps = ps; R.np = p->np; R.T = T; R.pdr_form = p->pdr_form; R.pf_max = p->pf_max;
+    R.pair_policy = p->pair_policy;
     R.seed = p->seed; R.run = p->run; R.t_begin = 1; R.t_end = T; R.flags = kFlagInit; R.g = 1;
     if (sched_tables(ps, p->pdr_form, T, &R.thr_dr, &R.thr_ah, &R.fsc, &R.nsc) != APO_OK)
         return fail(APO_ERR_CUDA, nullptr);

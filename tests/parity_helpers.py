@@ -36,7 +36,7 @@ def gpu_eval(apo, prob, X32):
 
 
 def compare_step(apo, orc, spec, ps, t, T, seed=0, np_=1, pf_max=0.1, pdr_form=0, state_seed=1,
-                 max_flip_frac=0.01, exact_f=False):
+                 max_flip_frac=0.01, exact_f=False, pair_policy=0):
     """One iteration from the same float32 state on both sides; returns a dict of
     counts.  Rows whose acceptance decision differs must be near-ties
     (|f_new - f_old| within tolerance); they are compared on the branch the GPU
@@ -47,8 +47,8 @@ def compare_step(apo, orc, spec, ps, t, T, seed=0, np_=1, pf_max=0.1, pdr_form=0
     F = orc.objective(oprob, X32.astype(np.float64))
     if spec.kind != 6:
         F = F.astype(np.float32)
-    gprm = apo.apo_params_make(ps, np_, pf_max, T, seed, 0, pdr_form)
-    oprm = orc.params(ps, np_, pf_max, T, seed, 0, pdr_form)
+    gprm = apo.apo_params_make(ps, np_, pf_max, T, seed, 0, pdr_form, pair_policy)
+    oprm = orc.params(ps, np_, pf_max, T, seed, 0, pdr_form, pair_policy)
     Xg, Fg = gpu_step(apo, gprob, gprm, t, X32, F)
     Xo, Fo, info = orc.apo_step(oprob, oprm, t, X32.astype(np.float64), np.asarray(F, np.float64),
                                 with_info=True)

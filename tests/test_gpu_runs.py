@@ -79,6 +79,29 @@ def test_end_to_end_best_fitness_over_seeds(apo, orc):
     assert abs(np.mean(g) - np.mean(o)) <= 4 * np.sqrt(np.var(g) / n + np.var(o) / n)
 
 
+@pytest.mark.parametrize("kind", [inputs.OBJ_ELLIPTIC, inputs.OBJ_ROSENBROCK])
+def test_median_best_over_31_seeds_within_one_percent(apo, orc, kind):
+    """The end-to-end criterion as stated: over seeds 0..30 the median best
+    fitness of the GPU runs is within 1% of the oracle's, on the unimodal forms
+    of the scale workload (D 100, shifted and rotated) at a population the
+    oracle finishes in seconds (ps 64, 300 iterations)."""
+    import os
+    import torch
+    spec = inputs.shifted_rotated(kind, 100, 1, run=kind)
+    ps, T, n = 64, 300, 31
+    probs = [apo.problem_from_spec(spec)] * n
+    prms = [apo.apo_params_make(ps, 1, 0.1, T, s) for s in range(n)]
+    bx = torch.zeros((n, 100), device="cuda")
+    bf = torch.zeros(n, dtype=torch.float64, device="cuda")
+    apo.apo_run_batch(probs, prms, bx, 100, bf)
+    g = bf.cpu().numpy()
+    oprob = orc.OracleProblem.from_spec(spec)
+    _, o = orc.apo_run_many([oprob] * n, [orc.params(ps, 1, 0.1, T, s) for s in range(n)], os.cpu_count() or 1)
+    gap = abs(np.median(g) - np.median(o)) / abs(np.median(o))
+    print("%s: median best gpu %.6g oracle %.6g (relative gap %.2e)" % (spec.name, np.median(g), np.median(o), gap))
+    assert gap <= 0.01
+
+
 def test_batch_equals_single_runs(apo):
     import torch
     specs = [(inputs.shifted_rotated(inputs.OBJ_RASTRIGIN, 10, 0), 20),
@@ -149,11 +172,12 @@ def test_lockstep_every_iteration_of_a_run(apo, orc, seed):
     within the tolerance, and a decision differs only where the oracle's own
     f difference is at the resolution of binary32 f.
 
-    Late in a run the foraging factor vanishes and many candidates differ from
-    their old rows by a few ulps, so how many near-ties a run meets depends on
-    its trajectory (measured with the FP32 FMA rotation: 10 to 224 flips per
-    1000 iterations over 16 seeds, every one with |df| <= 2.4e-6 |f|).  The
-    bound is therefore on where a flip may happen, not on how many."""
+    Late in a run the foraging factor vanishes and many candidates round, in
+    binary32, to their old rows: the GPU then evaluates the same point again and
+    (strict improvement) keeps the old row, while the float64 candidate may win
+    by a rounding error.  Such a decision changes no stored position.  Every
+    other differing decision counts as a flip, at most ceil(1% of ps) per
+    iteration (the near-tie reading)."""
     import torch
     from parity_helpers import tol
     spec = inputs.single_rastrigin(0)
@@ -182,7 +206,10 @@ def test_lockstep_every_iteration_of_a_run(apo, orc, seed):
         assert not np.any(diff & ~near), (t, np.nonzero(diff & ~near))
         res = np.abs(info["fnew"] - Fs) <= 1e-5 * np.maximum(np.abs(Fs), 1.0)
         assert not np.any(diff & ~res), (t, np.nonzero(diff & ~res))
-        flips += int(diff.sum())
+        same32 = np.all(info["xnew"].astype(np.float32) == Xh[info["order"]].astype(np.float32), axis=1)
+        it_flips = int((diff & ~same32).sum())
+        assert it_flips <= int(np.ceil(0.01 * ps)), (t, it_flips, np.nonzero(diff & ~same32))
+        flips += it_flips
         want_X = np.where(took[:, None], info["xnew"], Xh[info["order"]])
         want_F = np.where(took, info["fnew"], Fs)
         assert close(Xg, want_X).all(), t
@@ -223,3 +250,23 @@ def test_prepared_batch_autotune_and_graph_replay(apo):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(bf, ref_f) and torch.equal(bc, ref_c) and torch.equal(bx, ref_x)
+
+
+@pytest.mark.parametrize("side", [512, 1024, 2048, 4096])
+def test_single_threshold_at_the_papers_settings(apo, orc, side):
+    """The paper's thresholding settings (Sec. 5.2, Table 3): one threshold,
+    ps 100, 50 iterations, on a synthetic 8-bit image of side x side pixels
+    (the photograph is not available).  The device histogram is bit-exact and
+    APO's best threshold reaches the exhaustive optimum of sigma_B^2 over all
+    256 thresholds."""
+    import torch
+    img = inputs.gmm_images_torch(1, side, seed=side, device="cuda")
+    h = torch.empty((1, 256), dtype=torch.int32, device="cuda")
+    apo.apo_histogram_u8(img, side * side, 1, h)
+    torch.cuda.synchronize()
+    hist = np.bincount(img[0].cpu().numpy(), minlength=256)
+    np.testing.assert_array_equal(h[0].cpu().numpy(), hist)
+    prob = apo.apo_problem_create(1, np.zeros(1), np.full(1, 255.0), apo.APO_OBJ_OTSU, hist_device=h[0])
+    bx, bf, _ = apo.apo_run(prob, apo.apo_params_make(100, 1, 0.1, 50, side))
+    best = max(orc.otsu_sigma_b2(hist, np.array([t])) for t in range(256))
+    assert -bf == best
