@@ -59,8 +59,13 @@ typedef enum apo_objective_kind {
                                 with its own o_k, M_k, perm_k; weights
                                 w_k = exp(-||x-o_k||^2 / (2 D sigma_k^2));
                                 f = sum w_k (g_k + bias_k) / sum w_k                 */
-    APO_OBJ_OTSU = 6         /* -sigma_B^2 of an image histogram, thresholds
+    APO_OBJ_OTSU = 6,        /* -sigma_B^2 of an image histogram, thresholds
                                 t_j = clamp(floor(x_j), 0, 255) sorted (Sec. 5.2)     */
+    /* the further benchmark forms of Sec. 5.1 (Table 2), shifted and rotated: */
+    APO_OBJ_BENTCIGAR = 7,   /* z_1^2 + 10^6 sum_{i>=2} z_i^2                          */
+    APO_OBJ_HGBAT = 8,       /* y = z / 20 - 1: |(sum y^2)^2 - (sum y)^2|^(1/2)
+                                + (sum y^2 / 2 + sum y) / D + 1/2                     */
+    APO_OBJ_GRIEWANK = 9     /* y = 6 z: 1 + sum y_i^2 / 4000 - prod cos(y_i / sqrt(i)) */
 } apo_objective_kind;
 
 #define APO_MAX_COMPONENTS 10

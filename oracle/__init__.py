@@ -22,7 +22,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-OBJ_SPHERE, OBJ_ELLIPTIC, OBJ_ROSENBROCK, OBJ_RASTRIGIN, OBJ_HYBRID, OBJ_COMPOSITION, OBJ_OTSU = range(7)
+(OBJ_SPHERE, OBJ_ELLIPTIC, OBJ_ROSENBROCK, OBJ_RASTRIGIN, OBJ_HYBRID, OBJ_COMPOSITION, OBJ_OTSU,
+ OBJ_BENTCIGAR, OBJ_HGBAT, OBJ_GRIEWANK) = range(10)
 MODE_DORMANCY, MODE_REPRODUCTION, MODE_AUTOTROPHIC, MODE_HETEROTROPHIC = range(4)
 
 

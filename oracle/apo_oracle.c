@@ -139,7 +139,10 @@ enum {
     ORC_OBJ_RASTRIGIN = 3,
     ORC_OBJ_HYBRID = 4,
     ORC_OBJ_COMPOSITION = 5,
-    ORC_OBJ_OTSU = 6
+    ORC_OBJ_OTSU = 6,
+    ORC_OBJ_BENTCIGAR = 7,
+    ORC_OBJ_HGBAT = 8,
+    ORC_OBJ_GRIEWANK = 9
 };
 
 typedef struct {
@@ -218,6 +221,42 @@ static double orc_rastrigin(const double* z, int n)
     return s;
 }
 
+/* The benchmark forms of Sec. 5.1 (Table 2) that the other forms do not cover,
+ * written out from their textbook definitions (the CEC data files are not
+ * available; the scalings are the usual ones of those suites):
+ * Bent Cigar: z_1^2 + 10^6 sum_{i>=2} z_i^2. */
+static double orc_bent_cigar(const double* z, int n)
+{
+    double s = 0.0;
+    for (int i = 1; i < n; ++i) s += z[i] * z[i];
+    return z[0] * z[0] + 1e6 * s;
+}
+
+/* HGBat on y = z / 20 - 1 (optimum at z = 0):
+ * |(sum y^2)^2 - (sum y)^2|^(1/2) + (sum y^2 / 2 + sum y) / n + 1/2. */
+static double orc_hgbat(const double* z, int n)
+{
+    double s2 = 0.0, s1 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double y = z[i] * 0.05 - 1.0;
+        s2 += y * y;
+        s1 += y;
+    }
+    return sqrt(fabs(s2 * s2 - s1 * s1)) + (0.5 * s2 + s1) / (double)n + 0.5;
+}
+
+/* Griewank on y = 6 z: 1 + sum y_i^2 / 4000 - prod cos(y_i / sqrt(i)), i = 1..n. */
+static double orc_griewank(const double* z, int n)
+{
+    double s = 0.0, p = 1.0;
+    for (int i = 0; i < n; ++i) {
+        double y = 6.0 * z[i];
+        s += y * y;
+        p *= cos(y / sqrt((double)(i + 1)));
+    }
+    return 1.0 + s / 4000.0 - p;
+}
+
 /* Hybrid: w = z permuted by perm, split ceil(0.3 D) / ceil(0.3 D) / rest
  * across elliptic, Rosenbrock and Rastrigin. */
 static void orc_hybrid_sizes(int D, int* n1, int* n2, int* n3)
@@ -269,6 +308,9 @@ static double orc_basic_form(int form, int D, const float* M, const float* o,
     case ORC_OBJ_ROSENBROCK: f = orc_rosenbrock(z, D); break;
     case ORC_OBJ_RASTRIGIN: f = orc_rastrigin(z, D); break;
     case ORC_OBJ_HYBRID: f = orc_hybrid(z, perm, D); break;
+    case ORC_OBJ_BENTCIGAR: f = orc_bent_cigar(z, D); break;
+    case ORC_OBJ_HGBAT: f = orc_hgbat(z, D); break;
+    case ORC_OBJ_GRIEWANK: f = orc_griewank(z, D); break;
     default: f = NAN;
     }
     free(z);
@@ -369,6 +411,9 @@ double orc_objective(const orc_problem* P, const double* x)
     case ORC_OBJ_ROSENBROCK:
     case ORC_OBJ_RASTRIGIN:
     case ORC_OBJ_HYBRID:
+    case ORC_OBJ_BENTCIGAR:
+    case ORC_OBJ_HGBAT:
+    case ORC_OBJ_GRIEWANK:
         return orc_basic_form(P->kind, P->D, P->rot, P->shift, P->perm, x);
     case ORC_OBJ_COMPOSITION: return orc_composition(P, x);
     case ORC_OBJ_OTSU: return orc_otsu(P, x);

@@ -23,7 +23,7 @@ _lib = C.CDLL(LIB_PATH)
 
 APO_OK, APO_ERR_INVALID_ARG, APO_ERR_CUDA, APO_ERR_OOM, APO_ERR_TIMEOUT, APO_ERR_UNSUPPORTED, APO_ERR_INTERNAL = range(7)
 (APO_OBJ_SPHERE, APO_OBJ_ELLIPTIC, APO_OBJ_ROSENBROCK, APO_OBJ_RASTRIGIN, APO_OBJ_HYBRID,
- APO_OBJ_COMPOSITION, APO_OBJ_OTSU) = range(7)
+ APO_OBJ_COMPOSITION, APO_OBJ_OTSU, APO_OBJ_BENTCIGAR, APO_OBJ_HGBAT, APO_OBJ_GRIEWANK) = range(10)
 
 # every entry point declared in include/apo.h
 EXPORTS = ("apo_problem_create", "apo_problem_destroy", "apo_problem_dim", "apo_run", "apo_run_device",

@@ -160,7 +160,7 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
     *out = nullptr;
     if (!obj || !lb || !ub) { set_err("obj, lb and ub must not be NULL"); return APO_ERR_INVALID_ARG; }
     const int kind = obj->kind;
-    if (kind < APO_OBJ_SPHERE || kind > APO_OBJ_OTSU) { set_err("unknown objective kind %d", kind); return APO_ERR_INVALID_ARG; }
+    if (kind < APO_OBJ_SPHERE || kind > APO_OBJ_GRIEWANK) { set_err("unknown objective kind %d", kind); return APO_ERR_INVALID_ARG; }
     if (D < 1) { set_err("D must be >= 1"); return APO_ERR_INVALID_ARG; }
     if (kind == APO_OBJ_OTSU ? D > APO_MAX_OTSU_THRESHOLDS : D > APO_MAX_DIM) {
         set_err("D = %d exceeds the supported maximum", D);
@@ -300,11 +300,17 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
             s1 = n1; s2 = n1 + n2; nell = n1;
             break;
         }
-        default: break;
+        case APO_OBJ_BENTCIGAR: s1 = D; s2 = D; nell = 0; break;   // weights 1, 10^6, 10^6, ...
+        default: break;   // HGBat, Griewank: their own epilogue (form)
         }
         std::vector<float> ew(Dp, 1.f);
         for (int d = 0; d < nell; ++d)
             ew[d] = nell > 1 ? (float)std::pow(10.0, 6.0 * (double)d / (double)(nell - 1)) : 1.f;
+        if (form == APO_OBJ_BENTCIGAR)
+            for (int d = 1; d < D; ++d) ew[d] = 1e6f;
+        if (form == APO_OBJ_GRIEWANK)
+            for (int d = 0; d < D; ++d) ew[d] = (float)(1.0 / std::sqrt((double)(d + 1)));
+        comps[k].form = form;
         off_ew[k] = add(ew.data(), Dp * 4);
         comps[k].s1 = s1;
         comps[k].s2 = s2;

@@ -37,7 +37,7 @@ constexpr uint32_t kSlotMask = 0x7FFFFFFFu;
 
 enum Mode : int { kDormancy = 0, kReproduction = 1, kAutotrophic = 2, kHeterotrophic = 3 };
 enum Kind : int { kSphere = 0, kElliptic = 1, kRosenbrock = 2, kRastrigin = 3, kHybrid = 4,
-                  kComposition = 5, kOtsu = 6 };
+                  kComposition = 5, kOtsu = 6, kBentCigar = 7, kHGBat = 8, kGriewank = 9 };
 
 // Run flags.
 constexpr int kFlagInit = 1;      // initialise the population (t = 0)
@@ -45,8 +45,11 @@ constexpr int kFlagStepOut = 2;   // write the rank-ordered state to X_out / F_o
 constexpr int kFlagStateOut = 4;  // also write the state after t_end (current order) to X_out / F_out
 
 // One shifted-rotated component: z = M (x - o), then a segmented form:
-// [0, s1) elliptic with weights ew, [s1, s2) Rosenbrock chain, [s2, D) Rastrigin.
+// [0, s1) elliptic with weights ew, [s1, s2) Rosenbrock chain, [s2, D) Rastrigin
+// (sphere, elliptic, Bent Cigar, Rosenbrock, Rastrigin and hybrid are all of
+// this shape), or, by `form`, HGBat or Griewank (ew = 1 / sqrt(i)).
 struct DevComp {
+    int form;            // objective kind of the component
     const float* o;      // [Dp]
     const float* MT;     // [Dp][Np] transposed rotation, zero padded; nullptr = identity
     // The rotation for the tensor cores: B[k][n] = MT[k][n] * msc split into
@@ -250,6 +253,12 @@ __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_prod(float v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 __device__ __forceinline__ float warp_max(float v)

@@ -226,10 +226,45 @@ __device__ __forceinline__ void tile_gemm_f16x3(const float* __restrict__ Xc, in
     }
 }
 
+// HGBat of Sec. 5.1 from its per-row sums, with u = z / 20 (y = u - 1):
+// (sum y^2)^2 - (sum y)^2 = (sum y^2 + sum y)(sum y^2 - sum y) = a b with
+// a = sum u (u - 1) and b = sum (u - 1)(u - 2) = 3 a - 2 c + 2 D, c = sum u^2,
+// and (sum y^2 / 2 + sum y) / D + 1/2 = c / (2 D).  The same value as the
+// definition, without its cancellation near the optimum.
+__device__ __forceinline__ float hgbat_from_sums(float a, float c, int D)
+{
+    const float b = fmaf(3.f, a, fmaf(-2.f, c, 2.f * (float)D));
+    return sqrtf(fabsf(a * b)) + c / (2.f * (float)D);
+}
+
+// HGBat or Griewank (the forms that are not sums of per-coordinate terms) of
+// one row by one warp (z[d * zs]); Griewank uses y = 6 z and ew[d] = 1 / sqrt(d + 1).
+__device__ __forceinline__ float form2_value(const float* z, int zs, const DevComp& C, const float* ew, int D)
+{
+    const int lane = threadIdx.x & 31;
+    if (C.form == kHGBat) {
+        float a = 0.f, c = 0.f;
+        for (int d = lane; d < D; d += 32) {
+            const float u = z[(size_t)d * zs] * 0.05f;
+            a = fmaf(u, u, a - u);
+            c = fmaf(u, u, c);
+        }
+        return hgbat_from_sums(warp_sum(a), warp_sum(c), D);
+    }
+    float s = 0.f, p = 1.f;
+    for (int d = lane; d < D; d += 32) {
+        const float y = 6.f * z[(size_t)d * zs];
+        s = fmaf(y, y, s);
+        p *= cosf(y * ew[d]);
+    }
+    return fmaf(warp_sum(s), 1.f / 4000.f, 1.f - warp_prod(p));
+}
+
 // Segmented objective of one row by one warp (z[d * zs]): [0, s1) high-conditioned
 // elliptic, [s1, s2) chained Rosenbrock, [s2, D) Rastrigin cosine sum.
 __device__ __forceinline__ float seg_value(const float* z, int zs, const DevComp& C, const float* ew, int D)
 {
+    if (C.form == kHGBat || C.form == kGriewank) return form2_value(z, zs, C, ew, D);
     const int lane = threadIdx.x & 31;
     float s = 0.f;
     for (int d = lane; d < D; d += 32) {
@@ -256,6 +291,11 @@ template <int NR>
 __device__ __forceinline__ void seg_values(const float* const (&z)[NR], const DevComp& C, const float* ew, int D,
                                            float (&out)[NR])
 {
+    if (C.form == kHGBat || C.form == kGriewank) {
+#pragma unroll 1
+        for (int i = 0; i < NR; ++i) out[i] = form2_value(z[i], 1, C, ew, D);
+        return;
+    }
     const int lane = threadIdx.x & 31;
     float s[NR];
 #pragma unroll

@@ -1,0 +1,129 @@
+// apo_tma.cuh -- Tensor Memory Accelerator (TMA) tile loads, mbarrier waits
+// with time limits and tcgen05 operand descriptors for 128-byte-swizzled,
+// K-major fp16 tiles: the building blocks of the rotation GEMM of the
+// large-dimension path (apo_big.cu).
+//
+// A tile of R rows x 64 fp16 (128 bytes per row) is loaded by one
+// cp.async.bulk.tensor.2d with CU_TENSOR_MAP_SWIZZLE_128B: row r lands at
+// byte 128 r of the (1024-byte aligned) tile with its 16-byte chunks XORed by
+// r mod 8, which is the canonical K-major SWIZZLE_128B layout the tensor
+// cores read (8-row groups 1024 bytes apart).  A K step of 16 elements (32
+// bytes) inside the 64-wide tile advances the descriptor's start address by
+// 32 bytes; the hardware applies the swizzle to the computed addresses.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "apo_device.cuh"
+
+namespace apo {
+
+constexpr unsigned long long kTmaWaitNs = 1000000000ull;   // 1 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" : : "r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" : : "r"(bar), "r"(bytes) : "memory");
+}
+
+// Waits until the phase with the given parity of the mbarrier has completed;
+// false after the time limit.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    unsigned long long t0 = 0ull;
+    for (unsigned n = 0;; ++n) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((n & 255u) == 255u) {
+            const unsigned long long now = global_ns();
+            if (t0 == 0ull) t0 = now;
+            else if (now - t0 > kTmaWaitNs) return false;
+        }
+    }
+}
+
+// 2-D tiled TMA load of the box at (x = inner coordinate, y = row) into
+// shared memory, completing on the mbarrier's transaction count.  x must be a
+// multiple of 8 (16 bytes of fp16).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :
+        : "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_desc(const void* tmap)
+{
+    asm volatile("prefetch.tensormap [%0];" : : "l"(reinterpret_cast<uint64_t>(tmap)) : "memory");
+}
+
+// tcgen05 shared-memory descriptor of a K-major operand tile in the
+// SWIZZLE_128B layout at saddr (1024-byte aligned): 8-row groups 1024 bytes
+// apart (stride byte offset), leading byte offset unused (1), version 1,
+// swizzle mode 2 (128 bytes).
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;      // stride byte offset: 8 rows x 128 bytes
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16 with fp16 A and B (both K-major) and an
+// fp32 accumulator, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16_ss(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        :
+        : "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" : : "r"(bar)
+                 : "memory");
+}
+
+// 32 consecutive accumulator columns of the calling thread's TMEM lane
+// (warp w reads lanes 32 (w mod 4) .. + 31).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : : : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace apo

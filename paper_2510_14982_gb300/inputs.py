@@ -22,10 +22,11 @@ from typing import Optional
 
 import numpy as np
 
-OBJ_SPHERE, OBJ_ELLIPTIC, OBJ_ROSENBROCK, OBJ_RASTRIGIN, OBJ_HYBRID, OBJ_COMPOSITION, OBJ_OTSU = range(7)
+(OBJ_SPHERE, OBJ_ELLIPTIC, OBJ_ROSENBROCK, OBJ_RASTRIGIN, OBJ_HYBRID, OBJ_COMPOSITION, OBJ_OTSU,
+ OBJ_BENTCIGAR, OBJ_HGBAT, OBJ_GRIEWANK) = range(10)
 FORM_NAMES = {OBJ_SPHERE: "sphere", OBJ_ELLIPTIC: "elliptic", OBJ_ROSENBROCK: "rosenbrock",
               OBJ_RASTRIGIN: "rastrigin", OBJ_HYBRID: "hybrid", OBJ_COMPOSITION: "composition",
-              OBJ_OTSU: "otsu"}
+              OBJ_OTSU: "otsu", OBJ_BENTCIGAR: "bent_cigar", OBJ_HGBAT: "hgbat", OBJ_GRIEWANK: "griewank"}
 
 # stream ids keep unrelated draws independent of one another
 _S_SHIFT, _S_ROT, _S_PERM, _S_COMP, _S_SIZES, _S_IMAGE, _S_STATE = range(1, 8)
@@ -81,6 +82,16 @@ def shifted_rotated(kind: int, D: int, seed: int, run: int = 0, lb=-100.0, ub=10
     return ProblemSpec(kind=kind, D=D, lb=np.full(D, lb), ub=np.full(D, ub),
                        shift=shift(D, seed, run), rot=rotation(D, seed, run), perm=perm,
                        name=FORM_NAMES[kind])
+
+
+# The five forms of the paper's Table 2 (D = 1000): Bent Cigar, the
+# high-conditioned elliptic, HGBat, Rosenbrock and Griewank, each shifted and
+# rotated with its own seeded o and M.
+TABLE2_FORMS = (OBJ_BENTCIGAR, OBJ_ELLIPTIC, OBJ_HGBAT, OBJ_ROSENBROCK, OBJ_GRIEWANK)
+
+
+def table2_forms(seed: int = 0, D: int = 1000):
+    return [shifted_rotated(k, D, seed, run=k) for k in TABLE2_FORMS]
 
 
 def sphere(D: int, lb=0.0, ub=10.0) -> ProblemSpec:

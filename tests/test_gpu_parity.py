@@ -64,6 +64,12 @@ SPECS = [
     ("elliptic200", lambda: inputs.shifted_rotated(inputs.OBJ_ELLIPTIC, 200, 6)),
     ("composition20", lambda: inputs.composition(D=20, seed=7)),
     ("composition200", lambda: inputs.composition(D=200, seed=8)),
+    # the further forms of the paper's Table 2 at the sizes of the fused kernels
+    ("bent_cigar50", lambda: inputs.shifted_rotated(inputs.OBJ_BENTCIGAR, 50, 12)),
+    ("hgbat100", lambda: inputs.shifted_rotated(inputs.OBJ_HGBAT, 100, 13)),
+    ("griewank100", lambda: inputs.shifted_rotated(inputs.OBJ_GRIEWANK, 100, 14)),
+    ("griewank7_unrotated", lambda: inputs.ProblemSpec(kind=inputs.OBJ_GRIEWANK, D=7, lb=np.full(7, -100.0),
+                                                       ub=np.full(7, 100.0), shift=inputs.shift(7, 15))),
 ]
 
 
@@ -72,7 +78,8 @@ def test_objective_parity(apo, orc, name, mk):
     spec = mk()
     X = inputs.random_state(spec, 77, seed=3)
     # include the shift itself (f(o) = 0 for the zero-at-shift forms)
-    if spec.shift is not None and spec.kind in (inputs.OBJ_ELLIPTIC, inputs.OBJ_RASTRIGIN):
+    if spec.shift is not None and spec.kind in (inputs.OBJ_ELLIPTIC, inputs.OBJ_RASTRIGIN, inputs.OBJ_BENTCIGAR,
+                                                inputs.OBJ_HGBAT, inputs.OBJ_GRIEWANK):
         X[0] = spec.shift
     Fg = gpu_eval(apo, apo.problem_from_spec(spec), X)
     Fo = orc.objective(orc.OracleProblem.from_spec(spec), X.astype(np.float64))
@@ -134,6 +141,9 @@ STEP_CASES = [
      dict(np_=3)),
     ("d150_free_last_call", lambda: inputs.shifted_rotated(inputs.OBJ_ELLIPTIC, 150, 10), 128, 2, 100, {}),
     ("d100_np16", lambda: inputs.shifted_rotated(inputs.OBJ_RASTRIGIN, 100, 11), 256, 3, 100, dict(np_=16)),
+    ("bent_cigar50_ps200", lambda: inputs.shifted_rotated(inputs.OBJ_BENTCIGAR, 50, 16), 200, 3, 100, {}),
+    ("hgbat100_ps4096_grid", lambda: inputs.shifted_rotated(inputs.OBJ_HGBAT, 100, 17), 4096, 5, 1000, {}),
+    ("griewank30_ps64", lambda: inputs.shifted_rotated(inputs.OBJ_GRIEWANK, 30, 18), 64, 2, 100, {}),
 ]
 
 

@@ -130,3 +130,50 @@ def test_sphere_is_sum_of_squares(orc):
     spec = inputs.sphere(5, -10, 10)
     x = np.array([1.0, -2.0, 3.0, 0.5, 0.0])
     assert orc.objective(_prob(orc, spec), x)[0] == pytest.approx(14.25)
+
+
+@pytest.mark.parametrize("kind", [inputs.OBJ_BENTCIGAR, inputs.OBJ_HGBAT, inputs.OBJ_GRIEWANK])
+@pytest.mark.parametrize("D", [7, 1000])
+def test_table2_forms_vanish_at_the_shift(orc, kind, D):
+    """Bent Cigar, HGBat (y = z / 20 - 1 is -1 at z = 0) and Griewank are 0 at o."""
+    spec = inputs.shifted_rotated(kind, D, seed=3)
+    f = orc.objective(_prob(orc, spec), spec.shift.astype(np.float64))[0]
+    assert abs(f) < 1e-9
+
+
+def test_bent_cigar_weights_one_axis_by_one_and_the_rest_by_a_million(orc):
+    D = 9
+    spec = inputs.shifted_rotated(inputs.OBJ_BENTCIGAR, D, seed=4)
+    p = _prob(orc, spec)
+    for i in range(D):
+        z = np.zeros(D)
+        z[i] = 2.0
+        f = orc.objective(p, _x_for_z(spec, z))[0]
+        assert f == pytest.approx(4.0 if i == 0 else 4e6, rel=1e-9)
+
+
+@pytest.mark.parametrize("c", [2.0, -0.5, 3.0])
+def test_hgbat_on_a_constant_vector(orc, c):
+    """y_i = c for all i: Sum y^2 = D c^2, Sum y = D c, so
+    f = D |c| sqrt(|c^2 - 1|) + c^2 / 2 + c + 1/2 (z = 20 (1 + c))."""
+    D = 12
+    spec = inputs.shifted_rotated(inputs.OBJ_HGBAT, D, seed=5)
+    z = np.full(D, 20.0 * (1.0 + c))
+    f = orc.objective(_prob(orc, spec), _x_for_z(spec, z))[0]
+    want = D * abs(c) * np.sqrt(abs(c * c - 1.0)) + c * c / 2 + c + 0.5
+    assert f == pytest.approx(want, rel=1e-9)
+
+
+def test_griewank_product_takes_the_square_root_of_the_index(orc):
+    """y = 6 z with y_k / sqrt(k) = pi in coordinate k (1-based) and 0 elsewhere:
+    the product is cos(pi) = -1, so f = 1 + y_k^2 / 4000 + 1; the cosine period
+    pins sqrt(k) (an index without the root, or 0-based, gives another value)."""
+    D = 10
+    spec = inputs.shifted_rotated(inputs.OBJ_GRIEWANK, D, seed=6)
+    p = _prob(orc, spec)
+    for k in (1, 4, 9):
+        y = np.pi * np.sqrt(k)
+        z = np.zeros(D)
+        z[k - 1] = y / 6.0
+        f = orc.objective(p, _x_for_z(spec, z))[0]
+        assert f == pytest.approx(2.0 + y * y / 4000.0, rel=1e-9)
