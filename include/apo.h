@@ -69,7 +69,7 @@ typedef enum apo_objective_kind {
 } apo_objective_kind;
 
 #define APO_MAX_COMPONENTS 10
-#define APO_MAX_DIM 256
+#define APO_MAX_DIM 1024
 #define APO_MAX_OTSU_THRESHOLDS 31
 
 typedef struct apo_objective_desc {
@@ -118,7 +118,8 @@ int apo_effective_iterations(const apo_params* params);
 
 typedef struct apo_problem apo_problem;
 
-/* Creates a problem: D dimensions (1..APO_MAX_DIM; Otsu: 1..31 thresholds),
+/* Creates a problem: D dimensions (1..APO_MAX_DIM; Otsu: 1..31 thresholds;
+ * composition: 1..256),
  * bounds lb < ub per dimension (the Xmin, Xmax of Eq. 1-2), and the
  * objective.  Every array is copied to the device; the caller may free its
  * buffers on return.  Synchronous.  *out is NULL on failure. */
@@ -253,8 +254,12 @@ apo_status apo_evaluate(const apo_problem* prob, void* stream, const float* d_X,
 apo_status apo_clamp_eval_select(const apo_problem* prob, void* stream, int n, float* d_X,
                                  void* d_F, float* d_Xnew, void* d_Fnew);
 
-/* 256-bin histograms of n_images 8-bit images stored back to back
- * (d_pixels [n_images * n_pixels_per_image]) into d_hist [n_images*256]
+/* 256-bin histograms of n_images 8-bit images stored back to back, the first
+ * step of the thresholding application (Sec. 5.2: Otsu's between-class
+ * variance is a function of the image histogram only).  Counts are int32
+ * (bit-exact; every image has fewer than 2^31 pixels), not the int64 of the
+ * Otsu prefix sums, which apo_problem_create forms from them.  Input
+ * d_pixels [n_images * n_pixels_per_image], output d_hist [n_images*256]
  * (int32 counts, overwritten; bit-exact).  n_pixels_per_image < 2^31.
  * Stream-ordered. */
 apo_status apo_histogram_u8(const uint8_t* d_pixels, int64_t n_pixels_per_image, int n_images,
@@ -360,6 +365,26 @@ apo_status apo_philox4x32_10(const uint32_t* d_ctr, uint32_t key0, uint32_t key1
  * caller keeps ownership of the events. */
 apo_status apo_set_timing_events(void* before, void* after);
 
+/* Instrumentation of the large-dimension path (D > 256; no counterpart in
+ * the paper): with `on` != 0 every later run on that path brackets each
+ * stage launch with CUDA events on its stream and adds the elapsed device
+ * time per stage (0 ranking: chunk sort and rank; 1 candidate generation;
+ * 2 rotation GEMM with the objective epilogue; 3 greedy replacement), at
+ * the cost of a stream synchronisation at the end of each call.  Each call
+ * returns the totals since the previous one in ms[4] and launches[4] (either
+ * may be NULL), clears them and sets the switch.  Process-wide. */
+apo_status apo_large_stage_timing(int on, double* ms, long long* launches);
+
+/* Instrumentation (no counterpart in the paper): microbenchmarks of the
+ * pipes that bound the fused kernels, on the current device, every SM busy
+ * with independent dependency chains: FP32 fused multiply-add throughput
+ * (TFLOP/s, 2 flop per FMA), 32-bit integer multiply-add throughput (Tops/s)
+ * and plain integer ALU throughput (xor and add, Tops/s).  Outputs may be
+ * NULL.  Synchronous; allocates 64 bytes of device memory. */
+apo_status apo_measure_peaks(void* stream, double* ffma_tflops, double* imad_tops, double* alu_tops);
+
+/* Static text of a status code (never NULL).  The paper has no counterpart:
+ * the C ABI's error reporting convention. */
 const char* apo_status_string(apo_status status);
 const char* apo_last_error(void);
 

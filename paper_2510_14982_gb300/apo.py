@@ -34,7 +34,8 @@ EXPORTS = ("apo_problem_create", "apo_problem_destroy", "apo_problem_dim", "apo_
            "apo_mlp_create", "apo_mlp_destroy", "apo_mlp_set_params", "apo_mlp_get_params", "apo_mlp_forward",
            "apo_mlp_gradients", "apo_mlp_train",
            "apo_run_surrogate", "apo_surrogate_candidates", "apo_barrier_selftest",
-           "apo_philox4x32_10", "apo_set_timing_events", "apo_status_string", "apo_last_error")
+           "apo_philox4x32_10", "apo_set_timing_events", "apo_status_string", "apo_last_error",
+           "apo_measure_peaks", "apo_large_stage_timing")
 
 
 class apo_objective_desc(C.Structure):
@@ -121,6 +122,10 @@ for _f in ("apo_batch_create", "apo_batch_launch", "apo_batch_autotune",
            "apo_run", "apo_run_device", "apo_run_device_noalloc", "apo_run_batch", "apo_step", "apo_evaluate", "apo_clamp_eval_select",
            "apo_histogram_u8", "apo_philox4x32_10"):
     getattr(_lib, _f).restype = C.c_int
+_lib.apo_measure_peaks.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+_lib.apo_measure_peaks.restype = C.c_int
+_lib.apo_large_stage_timing.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+_lib.apo_large_stage_timing.restype = C.c_int
 _lib.apo_status_string.argtypes = [C.c_int]
 _lib.apo_status_string.restype = C.c_char_p
 _lib.apo_last_error.argtypes = []
@@ -430,3 +435,21 @@ def apo_barrier_selftest(launched: int, expected: int, rounds: int = 1, stream=N
 def raw_lib():
     """The loaded ctypes library (for callers that time the raw C entry points)."""
     return _lib
+
+
+def apo_measure_peaks(stream=None):
+    """apo_measure_peaks: measured FP32 FMA (TFLOP/s), IMAD and plain ALU (Tops/s) throughputs."""
+    f, i, a = C.c_double(), C.c_double(), C.c_double()
+    _check(_lib.apo_measure_peaks(_stream(stream), C.byref(f), C.byref(i), C.byref(a)), "apo_measure_peaks")
+    return {"ffma_tflops": f.value, "imad_tops": i.value, "alu_tops": a.value}
+
+
+LARGE_STAGES = ("rank", "generate", "gemm_eval", "greedy")
+
+
+def apo_large_stage_timing(on: bool):
+    """apo_large_stage_timing: the per-stage device ms and launch counts since the last call; sets the switch."""
+    ms = (C.c_double * 4)()
+    n = (C.c_longlong * 4)()
+    _check(_lib.apo_large_stage_timing(int(bool(on)), ms, n), "apo_large_stage_timing")
+    return {k: {"ms": ms[i], "launches": int(n[i])} for i, k in enumerate(LARGE_STAGES)}

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "libapo.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["apo_kernels.cu", "apo_api.cu", "apo_hist.cu", "apo_noalloc.cu", "apo_mlp.cu", "apo_surrogate.cu"]
+SOURCES = ["apo_kernels.cu", "apo_api.cu", "apo_hist.cu", "apo_noalloc.cu", "apo_mlp.cu", "apo_surrogate.cu",
+           "apo_big.cu", "apo_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-I", CSRC,
          "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "--expt-relaxed-constexpr"]

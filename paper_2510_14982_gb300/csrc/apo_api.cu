@@ -16,6 +16,7 @@
 #include <cuda_fp16.h>
 
 #include "../../include/apo.h"
+#include "apo_big.h"
 #include "apo_internal.h"
 #include "apo_plan.h"
 
@@ -65,6 +66,9 @@ constexpr size_t kBarStride = 256;
 cudaEvent_t g_ev_before = nullptr, g_ev_after = nullptr;
 
 }  // namespace
+
+cudaEvent_t apo::big_timing_before() { return g_ev_before; }
+cudaEvent_t apo::big_timing_after() { return g_ev_after; }
 
 
 // ------------------------------------------------------------ errors
@@ -166,6 +170,12 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
         set_err("D = %d exceeds the supported maximum", D);
         return APO_ERR_UNSUPPORTED;
     }
+    // dimensions above kSmallMaxDim take the large-dimension path
+    const bool big = D > kSmallMaxDim;
+    if (big && kind == APO_OBJ_COMPOSITION) {
+        set_err("the composition objective supports D <= %d", kSmallMaxDim);
+        return APO_ERR_UNSUPPORTED;
+    }
     for (int d = 0; d < D; ++d) {
         if (!std::isfinite(lb[d]) || !std::isfinite(ub[d]) || !(lb[d] < ub[d])) {
             set_err("bounds must be finite with lb < ub (dim %d)", d);
@@ -206,6 +216,7 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
 
     const int Dp = (D + 3) & ~3;
     const int Np = (D + 15) & ~15;
+    const int Kp = (D + 63) & ~63;
     const int bws = split_words(D);
     // Host image of every device array, laid out in one allocation.
     std::vector<std::pair<size_t, std::vector<unsigned char>>> pieces;
@@ -223,7 +234,7 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
     for (int d = 0; d < D; ++d) { lbf[d] = (float)lb[d]; ubf[d] = (float)ub[d]; }
     const size_t off_lb = add(lbf.data(), Dp * 4), off_ub = add(ubf.data(), Dp * 4);
     size_t off_o[kMaxComp] = {}, off_mt[kMaxComp] = {}, off_ew[kMaxComp] = {}, off_bh[kMaxComp] = {},
-           off_bl[kMaxComp] = {}, off_th[kMaxComp] = {}, off_tl[kMaxComp] = {};
+           off_bl[kMaxComp] = {}, off_th[kMaxComp] = {}, off_tl[kMaxComp] = {}, off_gh = 0, off_gl = 0;
     bool has_mt[kMaxComp] = {}, has_tc[kMaxComp] = {};
     DevComp comps[kMaxComp] = {};
     int any_rot = 0;
@@ -238,7 +249,36 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
         // z'_c = z_{perm[c]} for the hybrid form: rows of M are permuted, so
         // MT[j][c] = M[perm[c]][j]; otherwise MT = M^T.
         const bool perm_rows = form == APO_OBJ_HYBRID;
-        if (M || perm_rows) {
+        if (big) {
+            // the large-dimension GEMM operand: B = msc M' (M' = M with the
+            // hybrid's rows permuted, the identity when M is absent) split
+            // into fp16 hi + lo, row n = output dimension, K-contiguous [D][Kp]
+            double mmax = 0.0, ymax = 0.0;
+            if (M)
+                for (size_t i = 0; i < (size_t)D * D; ++i) mmax = std::max(mmax, (double)std::fabs(M[i]));
+            else
+                mmax = 1.0;
+            for (int d = 0; d < D; ++d)
+                ymax = std::max(ymax, std::max(std::fabs((double)ubf[d] - (double)o[d]),
+                                               std::fabs((double)lbf[d] - (double)o[d])));
+            const float msc = pow2_scale(mmax, 12), ysc = pow2_scale(ymax, 10);
+            std::vector<uint16_t> gh((size_t)D * Kp, 0), gl((size_t)D * Kp, 0);
+            for (int n = 0; n < D; ++n) {
+                const int row = perm_rows ? perm[n] : n;
+                for (int kk = 0; kk < D; ++kk) {
+                    const float v = (M ? M[(size_t)row * D + kk] : (kk == row ? 1.f : 0.f)) * msc;
+                    const __half hh = __float2half_rn(v);
+                    const __half ll = __float2half_rn(v - __half2float(hh));
+                    gh[(size_t)n * Kp + kk] = half_bits(hh);
+                    gl[(size_t)n * Kp + kk] = half_bits(ll);
+                }
+            }
+            off_gh = add(gh.data(), gh.size() * 2);
+            off_gl = add(gl.data(), gl.size() * 2);
+            comps[k].ysc = ysc;
+            comps[k].zsc = 1.f / (ysc * msc);
+            any_rot = 1;
+        } else if (M || perm_rows) {
             std::vector<float> mt((size_t)Dp * Np, 0.f);
             for (int c = 0; c < D; ++c) {
                 const int row = perm_rows ? perm[c] : c;
@@ -384,7 +424,7 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
     }
     DevProblem& dp = P->dev;
     std::memset(&dp, 0, sizeof(dp));
-    dp.D = D; dp.Dp = Dp; dp.Np = Np; dp.kind = kind; dp.ncomp = ncomp; dp.bws = bws;
+    dp.D = D; dp.Dp = Dp; dp.Np = Np; dp.kind = kind; dp.ncomp = ncomp; dp.bws = bws; dp.Kp = Kp;
     dp.lb = reinterpret_cast<const float*>(base + off_lb);
     dp.ub = reinterpret_cast<const float*>(base + off_ub);
     for (int k = 0; k < ncomp; ++k) {
@@ -396,6 +436,10 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
         dp.comp[k].Th = has_tc[k] ? reinterpret_cast<const uint4*>(base + off_th[k]) : nullptr;
         dp.comp[k].Tl = has_tc[k] ? reinterpret_cast<const uint4*>(base + off_tl[k]) : nullptr;
         dp.comp[k].ew = reinterpret_cast<const float*>(base + off_ew[k]);
+    }
+    if (big) {
+        dp.comp[0].Gh = reinterpret_cast<const uint16_t*>(base + off_gh);
+        dp.comp[0].Gl = reinterpret_cast<const uint16_t*>(base + off_gl);
     }
     if (kind == APO_OBJ_OTSU) {
         dp.P0 = reinterpret_cast<const long long*>(base + off_p0);
@@ -575,6 +619,10 @@ apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, b
         const RunSpec& s = specs_in[k];
         const int ps = s.prm.ps;
         const bool f64 = s.P->kind == APO_OBJ_OTSU;
+        if (s.P->D > kSmallMaxDim) {
+            set_err("prepared batches support D <= %d (run D = %d with apo_run_batch)", kSmallMaxDim, s.P->D);
+            return APO_ERR_UNSUPPORTED;
+        }
         // a lone run of a large population spreads over many CTAs
         const bool grid = ps > kQueueMaxPs || (n == 1 && ps >= kGridSingleMinPs);
         cls[k] = {grid, f64, f64 ? 1 : qpl_of(s.P)};
@@ -773,14 +821,58 @@ void release_prepared(Prepared& PR, cudaStream_t st)
     PR.ws = nullptr;
 }
 
-// Plans, allocates (stream-ordered) and launches a set of runs on one stream.
-apo_status launch_runs(std::vector<RunSpec>& specs, cudaStream_t st)
+// The large-dimension runs of a request (D > kSmallMaxDim), in groups of at
+// most kBigMaxRuns sharing (t_begin, t_end, flags), on the stage sequence of
+// apo_big.cu.
+apo_status launch_big_runs(const std::vector<RunSpec>& specs, cudaStream_t st)
 {
-    Prepared PR;
-    apo_status rc = prepare_runs(specs, st, true, 0, 0, &PR);
-    if (rc != APO_OK) return rc;
-    rc = launch_prepared(PR, st);
-    release_prepared(PR, st);
+    std::vector<BigSpec> all;
+    for (const RunSpec& s : specs) {
+        if (s.prm.ps > kBigMaxPs) {
+            set_err("ps = %d: the large-dimension path supports ps <= %d", s.prm.ps, kBigMaxPs);
+            return APO_ERR_UNSUPPORTED;
+        }
+        BigSpec b{};
+        b.P = s.P; b.prm = s.prm; b.ps = s.prm.ps; b.t_begin = s.t_begin; b.t_end = s.t_end;
+        b.flags = ((s.flags & kFlagInit) ? kBigInit : 0) | ((s.flags & kFlagStepOut) ? kBigStepOut : 0) |
+                  ((s.flags & kFlagStateOut) ? kBigStateOut : 0);
+        b.best_x = s.best_x; b.best_f = s.best_f; b.curve = s.curve;
+        b.X_in = s.X_in; b.F_in = static_cast<const float*>(s.F_in);
+        b.X_out = s.X_in; b.F_out = static_cast<float*>(s.F_in);
+        all.push_back(b);
+    }
+    std::vector<char> done(all.size(), 0);
+    for (size_t i = 0; i < all.size(); ++i) {
+        if (done[i]) continue;
+        std::vector<BigSpec> group;
+        for (size_t j = i; j < all.size() && (int)group.size() < kBigMaxRuns; ++j) {
+            if (done[j] || all[j].t_begin != all[i].t_begin || all[j].t_end != all[i].t_end ||
+                all[j].flags != all[i].flags)
+                continue;
+            group.push_back(all[j]);
+            done[j] = 1;
+        }
+        char msg[256] = "";
+        const apo_status rc = big_run_group(group, st, msg, sizeof(msg));
+        if (rc != APO_OK) { set_err("%s", msg); return rc; }
+    }
+    return APO_OK;
+}
+
+// Plans, allocates (stream-ordered) and launches a set of runs on one stream.
+apo_status launch_runs(std::vector<RunSpec>& specs_in, cudaStream_t st)
+{
+    std::vector<RunSpec> specs, big;
+    for (const RunSpec& s : specs_in) (s.P->D > kSmallMaxDim ? big : specs).push_back(s);
+    apo_status rc = APO_OK;
+    if (!specs.empty()) {
+        Prepared PR;
+        rc = prepare_runs(specs, st, true, 0, 0, &PR);
+        if (rc != APO_OK) return rc;
+        rc = launch_prepared(PR, st);
+        release_prepared(PR, st);
+    }
+    if (rc == APO_OK && !big.empty()) rc = launch_big_runs(big, st);
     return rc;
 }
 
@@ -1059,6 +1151,17 @@ apo_status eval_common(const apo_problem* P, void* stream, int n, const float* d
     if (!P || n < 0 || (n > 0 && (!d_X || !d_F))) { set_err("invalid evaluation arguments"); return APO_ERR_INVALID_ARG; }
     if (n == 0) return APO_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (P->D > kSmallMaxDim) {
+        if (select) { set_err("apo_clamp_eval_select supports D <= %d", kSmallMaxDim); return APO_ERR_UNSUPPORTED; }
+        if (n > kBigMaxPs) { set_err("at most %d rows per evaluation at D > %d", kBigMaxPs, kSmallMaxDim); return APO_ERR_UNSUPPORTED; }
+        BigSpec b{};
+        b.P = P; b.ps = n; b.flags = kBigEval; b.X_in = d_X; b.F_out = static_cast<float*>(d_F);
+        b.prm.ps = n; b.prm.np = 1; b.prm.max_iter = 1;
+        char msg[256] = "";
+        const apo_status rc = big_run_group(std::vector<BigSpec>{b}, st, msg, sizeof(msg));
+        if (rc != APO_OK) set_err("%s", msg);
+        return rc;
+    }
     ApoRun R;
     std::memset(&R, 0, sizeof(R));
     R.prob = P->dev;
@@ -1102,6 +1205,12 @@ extern "C" apo_status apo_histogram_u8(const uint8_t* d_pixels, int64_t n_pixels
     const cudaError_t e = launch_histogram_u8(d_pixels, n_pixels_per_image, n_images, d_hist,
                                               static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) { set_err("histogram launch failed: %s", cudaGetErrorString(e)); return APO_ERR_CUDA; }
+    return APO_OK;
+}
+
+extern "C" apo_status apo_large_stage_timing(int on, double* ms, long long* launches)
+{
+    big_stage_timing(on, ms, launches);
     return APO_OK;
 }
 

@@ -69,10 +69,22 @@ struct DevComp {
     int s1, s2;
     float inv_2Dsig2;    // 1 / (2 D sigma^2) (composition)
     float bias;          // composition bias
+    // The large-dimension path (D > kSmallMaxDim): the rotation's fp16 hi and
+    // lo parts of B = msc M (hybrid: rows permuted), row n = output dimension,
+    // K-contiguous [D][Kp], the B operand of the TMA-fed tcgen05 GEMM.
+    const uint16_t* Gh;
+    const uint16_t* Gl;
 };
+
+// Dimensions up to kSmallMaxDim run in the fused kernels (one warp holds a
+// whole row in registers); larger ones, up to kBigMaxDim, in the
+// large-dimension path.
+constexpr int kSmallMaxDim = 256;
+constexpr int kBigMaxDim = 1024;
 
 struct DevProblem {
     int D, Dp, Np, kind, ncomp;  // Dp = D rounded up to 4, Np = D rounded up to 16
+    int Kp;              // large-dimension path: D rounded up to 64
     int bws;             // words per column of Bh / Bl: split_words(D)
     const float* lb;     // [Dp]
     const float* ub;     // [Dp]

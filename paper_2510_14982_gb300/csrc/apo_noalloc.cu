@@ -102,6 +102,7 @@ extern "C" apo_status apo_run_device_noalloc(const apo_problem* P, const apo_par
     apo_params q;
     if (const char* why = normalize_params(p_in, &q)) return fail(APO_ERR_INVALID_ARG, why);
     const apo_params* p = &q;
+    if (P->D > kSmallMaxDim) return fail(APO_ERR_UNSUPPORTED, "apo_run_device_noalloc supports D <= 256");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device)
         return fail(APO_ERR_INVALID_ARG, "the problem belongs to another device");

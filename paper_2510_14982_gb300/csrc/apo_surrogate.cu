@@ -653,6 +653,7 @@ extern "C" apo_status apo_surrogate_candidates(const apo_problem* P, const apo_p
 {
     if (!P || !p_in || !d_X || !d_F || !d_Xcand) { apo::set_last_error("apo_surrogate_candidates: NULL argument"); return APO_ERR_INVALID_ARG; }
     if (P->kind == APO_OBJ_OTSU) { apo::set_last_error("apo_surrogate_candidates: float objectives only"); return APO_ERR_UNSUPPORTED; }
+    if (P->D > kSmallMaxDim) { apo::set_last_error("apo_surrogate_candidates: D <= 256 only"); return APO_ERR_UNSUPPORTED; }
     apo_params q;
     if (const char* why = normalize_params(p_in, &q)) { apo::set_last_error(why); return APO_ERR_INVALID_ARG; }
     const apo_params* p = &q;
@@ -733,6 +734,7 @@ extern "C" apo_status apo_run_surrogate(const apo_problem* P, const apo_params* 
 {
     if (!P || !p_in || !sp || !best_x || !best_f) { apo::set_last_error("apo_run_surrogate: NULL argument"); return APO_ERR_INVALID_ARG; }
     if (P->kind == APO_OBJ_OTSU) { apo::set_last_error("apo_run_surrogate: float objectives only"); return APO_ERR_UNSUPPORTED; }
+    if (P->D > kSmallMaxDim) { apo::set_last_error("apo_run_surrogate: D <= 256 only"); return APO_ERR_UNSUPPORTED; }
     apo_params q;
     if (const char* why = normalize_params(p_in, &q)) { apo::set_last_error(why); return APO_ERR_INVALID_ARG; }
     const apo_params* p = &q;

@@ -58,5 +58,5 @@ def test_argument_validation_without_gpu(libpath):
         apo.apo_problem_create(4, -np.ones(4), np.ones(4), apo.APO_OBJ_HYBRID, perm=np.array([0, 0, 1, 2]))
     assert e.value.status == apo.APO_ERR_INVALID_ARG
     with pytest.raises(apo.ApoError) as e:
-        apo.apo_problem_create(300, -np.ones(300), np.ones(300), apo.APO_OBJ_SPHERE)
+        apo.apo_problem_create(1025, -np.ones(1025), np.ones(1025), apo.APO_OBJ_SPHERE)
     assert e.value.status == apo.APO_ERR_UNSUPPORTED
