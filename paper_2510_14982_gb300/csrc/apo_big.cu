@@ -213,6 +213,22 @@ __global__ void __launch_bounds__(256) big_gen_kernel(const BigRun* __restrict__
     const float2* xa = reinterpret_cast<const float2*>(big_row(R, sa));
     const float2* xb = reinterpret_cast<const float2*>(big_row(R, sb));
     const float w1 = forage ? expf(-fabsf(R.F[sa] / (R.F[sb] + kEps))) : 0.f;
+    // The pairs a pass needs are requested one pass ahead (the first before
+    // the draws), so their latency overlaps arithmetic; lanes past D load the
+    // last pair (in bounds) and discard it.  The mode decides which rows are
+    // read at all (dormancy reads none).
+    const int qmax = ((D + 1) >> 1) - 1;
+    float2 ni = make_float2(0.f, 0.f), nj = ni, na2 = ni, nb2 = ni;
+    auto request = [&](int j) {
+        const int q = min(lane + 32 * j, qmax);
+        if (mode != kDormancy) ni = __ldcg(xi + q);
+        if (forage) {
+            na2 = __ldcg(xa + q);
+            nb2 = __ldcg(xb + q);
+            if (mode == kAutotrophic) nj = __ldcg(xj + q);
+        }
+    };
+    request(0);
 
     // per-dimension draws: Rand_d (A) and the mask keys (B) of the whole row
     uint32_t A[2 * kBigQPL], B[2 * kBigQPL];
@@ -245,15 +261,16 @@ __global__ void __launch_bounds__(256) big_gen_kernel(const BigRun* __restrict__
     uint32_t* yl = reinterpret_cast<uint32_t*>(R.Yl + (size_t)r * R.Kp);
 #pragma unroll
     for (int j = 0; j < kBigQPL; ++j) {
+        if (32 * j > qmax) break;   // warp-uniform: no lane has a pair here
+        const float2 vi = ni, vjl = nj, va = na2, vb = nb2;
+        if (32 * (j + 1) <= qmax) request(j + 1);
         const int q = lane + 32 * j;
         if (2 * q >= D) continue;
-        const float2 vi = __ldcg(xi + q);
         float2 acc = make_float2(0.f, 0.f);
         float2 vj = vi;
         if (forage) {
-            const float2 va = __ldcg(xa + q), vb = __ldcg(xb + q);
             acc = make_float2(w1 * (va.x - vb.x), w1 * (va.y - vb.y));
-            if (mode == kAutotrophic) vj = __ldcg(xj + q);
+            if (mode == kAutotrophic) vj = vjl;
             for (int k = 2; k <= np; ++k) {
                 uint32_t ea, eb;
                 if (mode == kAutotrophic) {
@@ -383,9 +400,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     big_gemm_kernel(const BigRun* __restrict__ runs, const __grid_constant__ BigMaps maps)
 {
     using Cfg = GemmCfg<BN>;
+    // N tiles vary fastest, so the CTAs that share an A tile run together and
+    // read it from L2 rather than HBM
     const int run = blockIdx.z;
     const BigRun& R = runs[run];
-    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
     if (m0 >= R.ps || n0 >= R.D) return;
     extern __shared__ unsigned char gemm_dyn[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -503,7 +522,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             if (n0 + 32 * cb < E.D) epi_terms(z, n0 + 32 * cb, E, ew_s, n0, s1, s2, prev, have_prev);
         }
         if (row < R.ps) {
-            const size_t o = (size_t)row * R.ntiles + blockIdx.y;
+            const size_t o = (size_t)row * R.ntiles + blockIdx.x;
             R.part[o] = make_float2(s1, s2);
             R.zedge[o] = make_float2(zfirst, prev);   // z at n0 and at the tile's last column
         }
@@ -662,7 +681,7 @@ cudaError_t launch_gemm(const BigRun* d_runs, const BigMaps& maps, int n_runs, i
     const int smem = kGemmSmem + 1024;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((max_ps + kBM - 1) / kBM, max_ntiles, n_runs);
+    dim3 grid(max_ntiles, (max_ps + kBM - 1) / kBM, n_runs);
     fn<<<grid, kGemmThreads, smem, st>>>(d_runs, maps);
     return cudaGetLastError();
 }
