@@ -348,8 +348,8 @@ extern "C" apo_status apo_problem_create(int D, const double* lb, const double* 
             ew[d] = nell > 1 ? (float)std::pow(10.0, 6.0 * (double)d / (double)(nell - 1)) : 1.f;
         if (form == APO_OBJ_BENTCIGAR)
             for (int d = 1; d < D; ++d) ew[d] = 1e6f;
-        if (form == APO_OBJ_GRIEWANK)
-            for (int d = 0; d < D; ++d) ew[d] = (float)(1.0 / std::sqrt((double)(d + 1)));
+        if (form == APO_OBJ_GRIEWANK)   // cos(y / sqrt(i)) = cospi(y / (pi sqrt(i)))
+            for (int d = 0; d < D; ++d) ew[d] = (float)(1.0 / (M_PI * std::sqrt((double)(d + 1))));
         comps[k].form = form;
         off_ew[k] = add(ew.data(), Dp * 4);
         comps[k].s1 = s1;

@@ -37,6 +37,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -53,7 +54,10 @@ constexpr int kGenWarps = 8;
 constexpr int kBM = 128;                    // GEMM tile rows (candidates)
 constexpr int kBK = 64;                     // GEMM K block: 64 fp16 = 128 bytes
 constexpr int kSortChunk = 1024;            // keys per sorted chunk
-constexpr int kGemmThreads = 128;
+// 16 warps: warp 0 lane 0 issues the TMA loads, warp 1 lane 0 the MMAs; in
+// the epilogue warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its candidate
+// rows) and the column quarter w / 4 of the tile
+constexpr int kGemmThreads = 512;
 constexpr int kGemmSmem = 192 * 1024;       // operand stages
 constexpr int kTileA = kBM * kBK * 2;       // bytes of one A part tile
 
@@ -162,12 +166,27 @@ __global__ void __launch_bounds__(1024) big_rank_kernel(const BigRun* __restrict
 // dormancy (Eq. 1), reproduction (Eq. 2), autotrophic (Eq. 6-7) or
 // heterotrophic (Eq. 8-10) foraging, the clamp; the same draw contract as the
 // fused kernels (counter (t, r, d, slot)).
-__global__ void __launch_bounds__(256) big_gen_kernel(const BigRun* __restrict__ runs, int t)
+// The rows a candidate reads (X_i, and X_j and the pair for foraging) are
+// staged in the warp's slice of shared memory by bulk copies
+// (cp.async.bulk, the TMA's untiled mode) issued before the draws, so that
+// up to 16 KB per warp are in flight while the Philox draws and the mask
+// selection run (the populations at ps 10000 do not fit L2, and row gathers
+// from HBM are latency-bound otherwise).
+__global__ void __launch_bounds__(256, 1) big_gen_kernel(const BigRun* __restrict__ runs, int t)
 {
+    extern __shared__ __align__(16) unsigned char gen_dyn[];
+    __shared__ __align__(8) unsigned long long row_bar[kGenWarps];
     const BigRun& R = runs[blockIdx.y];
-    const int lane = threadIdx.x & 31;
-    const int r = blockIdx.x * kGenWarps + (threadIdx.x >> 5);
-    if (r >= R.ps) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = blockIdx.x * kGenWarps + warp;
+    if (r >= R.ps) return;   // warp-uniform; the barrier below is the warp's own
+    const uint32_t bar = smem_u32(&row_bar[warp]);
+    float* rows_s = reinterpret_cast<float*>(gen_dyn) + (size_t)warp * 4 * R.Dp;   // X_i, X_a, X_b, X_j
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" : : : "memory");
+    }
+    __syncwarp();
     const int D = R.D, ps = R.ps, np = R.np;
     const uint32_t seed = R.seed, run = R.run;
     const uint32_t* perm = R.perm[t & 1];
@@ -208,27 +227,24 @@ __global__ void __launch_bounds__(256) big_gen_kernel(const BigRun* __restrict__
         sa = perm[r - 1 < 0 ? 0 : r - 1];
         sb = perm[r + 1 > ps - 1 ? ps - 1 : r + 1];
     }
-    const float2* xi = reinterpret_cast<const float2*>(big_row(R, si));
-    const float2* xj = reinterpret_cast<const float2*>(big_row(R, sj));
-    const float2* xa = reinterpret_cast<const float2*>(big_row(R, sa));
-    const float2* xb = reinterpret_cast<const float2*>(big_row(R, sb));
     const float w1 = forage ? expf(-fabsf(R.F[sa] / (R.F[sb] + kEps))) : 0.f;
-    // The pairs a pass needs are requested one pass ahead (the first before
-    // the draws), so their latency overlaps arithmetic; lanes past D load the
-    // last pair (in bounds) and discard it.  The mode decides which rows are
-    // read at all (dormancy reads none).
-    const int qmax = ((D + 1) >> 1) - 1;
-    float2 ni = make_float2(0.f, 0.f), nj = ni, na2 = ni, nb2 = ni;
-    auto request = [&](int j) {
-        const int q = min(lane + 32 * j, qmax);
-        if (mode != kDormancy) ni = __ldcg(xi + q);
-        if (forage) {
-            na2 = __ldcg(xa + q);
-            nb2 = __ldcg(xb + q);
-            if (mode == kAutotrophic) nj = __ldcg(xj + q);
-        }
-    };
-    request(0);
+    // the rows the mode reads, by bulk copy into the warp's slice (dormancy reads none)
+    const int nrows = mode == kDormancy ? 0 : (mode == kReproduction ? 1 : (mode == kHeterotrophic ? 3 : 4));
+    const uint32_t row_bytes = (uint32_t)R.Dp * 4u;
+    if (lane == 0 && nrows > 0) {
+        const uint32_t slots[4] = {si, sa, sb, sj};
+        mbar_expect_tx(bar, row_bytes * (uint32_t)nrows);
+        for (int k = 0; k < nrows; ++k)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                :
+                : "r"(smem_u32(rows_s + (size_t)k * R.Dp)), "l"(big_row(R, slots[k])), "r"(row_bytes), "r"(bar)
+                : "memory");
+    }
+    const float2* xi = reinterpret_cast<const float2*>(rows_s);
+    const float2* xa = reinterpret_cast<const float2*>(rows_s + R.Dp);
+    const float2* xb = reinterpret_cast<const float2*>(rows_s + 2 * R.Dp);
+    const float2* xj = reinterpret_cast<const float2*>(rows_s + 3 * R.Dp);
 
     // per-dimension draws: Rand_d (A) and the mask keys (B) of the whole row
     uint32_t A[2 * kBigQPL], B[2 * kBigQPL];
@@ -255,70 +271,92 @@ __global__ void __launch_bounds__(256) big_gen_kernel(const BigRun* __restrict__
     const float ff = forage ? u01(sc.y) * fsc : 0.f;
     const float sg = sign_draw(sc.z);
     const float rho = u01(sc.w);
+    if (nrows > 0 && !mbar_wait(bar, 0u)) {
+        // the copies did not land within the limit: report, and let them land
+        // (bounded) before the warp's shared memory is released
+        if (lane == 0) set_status(R.status, 4 /* APO_ERR_TIMEOUT */);
+        mbar_wait(bar, 0u);
+        return;
+    }
 
     float2* xc = reinterpret_cast<float2*>(R.X[R.loc[si] ^ 1u] + (size_t)si * R.Dp);
     uint32_t* yh = reinterpret_cast<uint32_t*>(R.Yh + (size_t)r * R.Kp);
     uint32_t* yl = reinterpret_cast<uint32_t*>(R.Yl + (size_t)r * R.Kp);
-#pragma unroll
-    for (int j = 0; j < kBigQPL; ++j) {
-        if (32 * j > qmax) break;   // warp-uniform: no lane has a pair here
-        const float2 vi = ni, vjl = nj, va = na2, vb = nb2;
-        if (32 * (j + 1) <= qmax) request(j + 1);
-        const int q = lane + 32 * j;
-        if (2 * q >= D) continue;
-        float2 acc = make_float2(0.f, 0.f);
-        float2 vj = vi;
-        if (forage) {
-            acc = make_float2(w1 * (va.x - vb.x), w1 * (va.y - vb.y));
-            if (mode == kAutotrophic) vj = vjl;
-            for (int k = 2; k <= np; ++k) {
-                uint32_t ea, eb;
-                if (mode == kAutotrophic) {
-                    // pair k's draws (lanes may have left the loop: no shuffle)
-                    const uint4 pr = philox((uint32_t)t, (uint32_t)r, (uint32_t)(k - 1), kSlotPair, seed, run);
-                    ea = perm[idx_draw(pr.x, na)];
-                    eb = perm[ob + idx_draw(pr.y, nb)];
-                } else {
-                    ea = perm[r - k < 0 ? 0 : r - k];
-                    eb = perm[r + k > ps - 1 ? ps - 1 : r + k];
-                }
-                const float w2 = expf(-fabsf(R.F[ea] / (R.F[eb] + kEps)));
-                const float2 qa = __ldcg(reinterpret_cast<const float2*>(big_row(R, ea)) + q);
-                const float2 qb = __ldcg(reinterpret_cast<const float2*>(big_row(R, eb)) + q);
-                acc.x = fmaf(w2, qa.x - qb.x, acc.x);
-                acc.y = fmaf(w2, qa.y - qb.y, acc.y);
-            }
-        }
-        float out[2];
-        const float x0s[2] = {vi.x, vi.y}, xjs[2] = {vj.x, vj.y}, accs[2] = {acc.x, acc.y};
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int d = 2 * q + e;
-            const int sl = 2 * j + e;
-            const int dc = d < D ? d : D - 1;
-            const float lb = R.lb[dc], ub = R.ub[dc];
-            const float x0 = x0s[e];
-            float x;
-            if (mode == kDormancy) {
-                x = fmaf(u01(A[sl]), ub - lb, lb);                                  // Eq. 1
+    // bounds and shift as pairs (Dp is a multiple of 4; the padding past D is
+    // zero, so the operand's padding comes out as ysc (0 - 0) = 0)
+    const float2* lb2 = reinterpret_cast<const float2*>(R.lb);
+    const float2* ub2 = reinterpret_cast<const float2*>(R.ub);
+    const float2* o2 = reinterpret_cast<const float2*>(R.o);
+    const float ysc = R.ysc;
+    // Extra pairs (np > 1, Eq. 6-10) added to acc for the pair (2q, 2q + 1).
+    auto more_pairs = [&](int q, float2& acc, bool autot) {
+        for (int k = 2; k <= np; ++k) {
+            uint32_t ea, eb;
+            if (autot) {
+                const uint4 pr = philox((uint32_t)t, (uint32_t)r, (uint32_t)(k - 1), kSlotPair, seed, run);
+                ea = perm[idx_draw(pr.x, na)];
+                eb = perm[ob + idx_draw(pr.y, nb)];
             } else {
-                if (mode == kReproduction) x = x0 + sg * rho * fmaf(u01(A[sl]), ub - lb, lb);   // Eq. 2
-                else if (mode == kAutotrophic) x = x0 + ff * (xjs[e] - x0 + accs[e] * inv_np);  // Eq. 6
-                else {
-                    const float xnear = (1.f + sg * u01(A[sl]) * nsc) * x0;                    // Eq. 9
-                    x = x0 + ff * (xnear - x0 + accs[e] * inv_np);                              // Eq. 8
-                }
-                x = ((mask >> sl) & 1u) ? x : x0;                                               // Eq. 3, 5
+                ea = perm[r - k < 0 ? 0 : r - k];
+                eb = perm[r + k > ps - 1 ? ps - 1 : r + k];
             }
-            out[e] = d < D ? fminf(fmaxf(x, lb), ub) : 0.f;
+            const float w2 = expf(-fabsf(R.F[ea] / (R.F[eb] + kEps)));
+            const float2 qa = __ldcg(reinterpret_cast<const float2*>(big_row(R, ea)) + q);
+            const float2 qb = __ldcg(reinterpret_cast<const float2*>(big_row(R, eb)) + q);
+            acc.x = fmaf(w2, qa.x - qb.x, acc.x);
+            acc.y = fmaf(w2, qa.y - qb.y, acc.y);
         }
-        xc[q] = make_float2(out[0], out[1]);
-        const int d1 = min(2 * q + 1, D - 1);
-        uint32_t h, l;
-        // past D the operand is zero: y = ysc (o - o)
-        split_y(out[0], 2 * q + 1 < D ? out[1] : R.o[d1], R.o[2 * q], R.o[d1], R.ysc, h, l);
-        yh[q] = h;
-        yl[q] = l;
+    };
+    // The candidate, one unrolled pass loop per mode (no per-element mode
+    // branch); lanes past D skip their pair.
+    auto emit = [&](auto mode_c) {
+        constexpr int M = decltype(mode_c)::value;
+#pragma unroll
+        for (int j = 0; j < kBigQPL; ++j) {
+            const int q = lane + 32 * j;
+            if (2 * q >= D) continue;
+            const float2 lb = __ldg(lb2 + q), ub = __ldg(ub2 + q), o = __ldg(o2 + q);
+            float2 x;
+            if constexpr (M == kDormancy) {
+                x.x = fmaf(u01(A[2 * j]), ub.x - lb.x, lb.x);                        // Eq. 1
+                x.y = fmaf(u01(A[2 * j + 1]), ub.y - lb.y, lb.y);
+            } else {
+                const float2 x0 = xi[q];
+                if constexpr (M == kReproduction) {
+                    x.x = x0.x + sg * rho * fmaf(u01(A[2 * j]), ub.x - lb.x, lb.x);  // Eq. 2
+                    x.y = x0.y + sg * rho * fmaf(u01(A[2 * j + 1]), ub.y - lb.y, lb.y);
+                } else {
+                    const float2 va = xa[q], vb = xb[q];
+                    float2 acc = make_float2(w1 * (va.x - vb.x), w1 * (va.y - vb.y));
+                    if (np > 1) more_pairs(q, acc, M == kAutotrophic);
+                    if constexpr (M == kAutotrophic) {
+                        const float2 vj = xj[q];
+                        x.x = x0.x + ff * (vj.x - x0.x + acc.x * inv_np);           // Eq. 6
+                        x.y = x0.y + ff * (vj.y - x0.y + acc.y * inv_np);
+                    } else {
+                        const float nx = (1.f + sg * u01(A[2 * j]) * nsc) * x0.x;      // Eq. 9
+                        const float ny = (1.f + sg * u01(A[2 * j + 1]) * nsc) * x0.y;
+                        x.x = x0.x + ff * (nx - x0.x + acc.x * inv_np);              // Eq. 8
+                        x.y = x0.y + ff * (ny - x0.y + acc.y * inv_np);
+                    }
+                }
+                x.x = ((mask >> (2 * j)) & 1u) ? x.x : x0.x;                          // Eq. 3, 5
+                x.y = ((mask >> (2 * j + 1)) & 1u) ? x.y : x0.y;
+            }
+            x.x = fminf(fmaxf(x.x, lb.x), ub.x);
+            x.y = 2 * q + 1 < D ? fminf(fmaxf(x.y, lb.y), ub.y) : 0.f;
+            xc[q] = x;
+            uint32_t h, l;
+            split_y(x.x, x.y, o.x, o.y, ysc, h, l);
+            yh[q] = h;
+            yl[q] = l;
+        }
+    };
+    switch (mode) {
+    case kDormancy: emit(std::integral_constant<int, kDormancy>{}); break;
+    case kReproduction: emit(std::integral_constant<int, kReproduction>{}); break;
+    case kAutotrophic: emit(std::integral_constant<int, kAutotrophic>{}); break;
+    default: emit(std::integral_constant<int, kHeterotrophic>{}); break;
     }
 }
 
@@ -363,11 +401,12 @@ struct EpiForm {
     int D, form, s1, s2;
 };
 
-__device__ __forceinline__ void epi_terms(const float (&z)[32], int n, const EpiForm& E, const float* ew_s, int n0,
+template <int W>
+__device__ __forceinline__ void epi_terms(const float (&z)[W], int n, const EpiForm& E, const float* ew_s, int n0,
                                           float& s1, float& s2, float& prev, bool& have_prev)
 {
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
+    for (int i = 0; i < W; ++i) {
         const int c = n + i;
         if (c >= E.D) break;
         const float v = z[i];
@@ -378,7 +417,7 @@ __device__ __forceinline__ void epi_terms(const float (&z)[32], int n, const Epi
         } else if (E.form == kGriewank) {
             const float y = 6.f * v;
             s1 = fmaf(y, y, s1);
-            s2 *= cosf(y * ew_s[c - n0]);
+            s2 *= cospif(y * ew_s[c - n0]);   // ew = 1 / (pi sqrt(c + 1))
         } else if (c < E.s1) {
             s1 = fmaf(ew_s[c - n0] * v, v, s1);
         } else if (c < E.s2) {
@@ -412,6 +451,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     __shared__ __align__(8) unsigned long long full_bar[Cfg::kStages], empty_bar[Cfg::kStages], done_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ float ew_s[BN];
+    __shared__ float2 s_quart[4][kBM], s_edge[4][kBM];
     __shared__ int s_err;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = (R.D + kBK - 1) / kBK;
@@ -495,39 +535,74 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         umma_commit(smem_u32(&done_bar));
     }
     __syncwarp();
-    // epilogue: thread = candidate row m0 + 32 warp + lane
+    // epilogue: warp w takes candidate rows m0 + 32 (w mod 4) + lane (its TMEM
+    // lanes) and the column quarter w / 4 (SW = BN / 4 columns); the four
+    // quarters of a row are then combined in column order through shared memory
+    constexpr int SW = BN / 4;
+    const int quarter = warp & 3, split = warp >> 2;
     const bool ok = mbar_wait(smem_u32(&done_bar), 0u) && atomicAdd(&s_err, 0) == 0;
     asm volatile("tcgen05.fence::after_thread_sync;" : : : "memory");
-    const int row = m0 + 32 * warp + lane;
+    const int rt = 32 * quarter + lane, row = m0 + rt;
+    const int c0 = n0 + SW * split;
     const EpiForm E{R.D, R.form, R.s1, R.s2};
     float s1 = 0.f, s2 = E.form == kGriewank ? 1.f : 0.f, prev = 0.f;
     bool have_prev = false;
     float zfirst = 0.f;
     const float zsc = R.zsc;
-    if (__all_sync(0xffffffffu, ok)) {
-#pragma unroll 1
-        for (int cb = 0; cb < BN / 32; ++cb) {
-            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * cb);
-            float z[32], v[32];
-            tmem_ld32(ta, z);   // corrections
-            const int used = nk < kMainAcc ? nk : kMainAcc;
-            for (int a = 0; a < used; ++a) {
-                tmem_ld32(ta + (uint32_t)(BN * (1 + a)), v);
+    const bool all_ok = __syncthreads_and(ok) != 0;
+    if (all_ok) {
+        const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(SW * split);
+        const int used = nk < kMainAcc ? nk : kMainAcc;
+        uint32_t r0[SW], r1[SW];
+        float z[SW];
+        tmem_ld_nowait(ta, r0);                              // corrections
+        tmem_ld_nowait(ta + (uint32_t)BN, r1);               // main accumulator 0
+        tmem_wait(r0, r1);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) z[i] += v[i];
-            }
+        for (int i = 0; i < SW; ++i) z[i] = __uint_as_float(r0[i]) + __uint_as_float(r1[i]);
+        if (used > 1) {
+            tmem_ld_nowait(ta + (uint32_t)(2 * BN), r0);
+            if (used > 2) tmem_ld_nowait(ta + (uint32_t)(3 * BN), r1);
+            tmem_wait(r0, r1);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) z[i] *= zsc;
-            if (cb == 0) zfirst = z[0];
-            if (n0 + 32 * cb < E.D) epi_terms(z, n0 + 32 * cb, E, ew_s, n0, s1, s2, prev, have_prev);
+            for (int i = 0; i < SW; ++i) z[i] += __uint_as_float(r0[i]) + (used > 2 ? __uint_as_float(r1[i]) : 0.f);
         }
-        if (row < R.ps) {
-            const size_t o = (size_t)row * R.ntiles + blockIdx.x;
-            R.part[o] = make_float2(s1, s2);
-            R.zedge[o] = make_float2(zfirst, prev);   // z at n0 and at the tile's last column
-        }
+#pragma unroll
+        for (int i = 0; i < SW; ++i) z[i] *= zsc;
+        zfirst = z[0];
+        if (c0 < E.D) epi_terms<SW>(z, c0, E, ew_s, n0, s1, s2, prev, have_prev);
+        s_quart[split][rt] = make_float2(s1, s2);
+        s_edge[split][rt] = make_float2(zfirst, prev);
     } else if (threadIdx.x == 0) {
         set_status(R.status, 4 /* APO_ERR_TIMEOUT */);
+    }
+    __syncthreads();
+    if (all_ok && split == 0 && row < R.ps) {
+        // quarters in column order; the Rosenbrock pair (n, n + 1) across a
+        // quarter boundary is added here
+        float a = s_quart[0][rt].x, b = s_quart[0][rt].y;
+        float zl = s_edge[0][rt].y;
+        for (int c = 1; c < 4 && n0 + SW * c < E.D; ++c) {
+            const float2 q = s_quart[c][rt];
+            const float2 ed = s_edge[c][rt];
+            if (E.form == kGriewank) {
+                a += q.x;
+                b *= q.y;
+            } else {
+                a += q.x;
+                b += q.y;
+            }
+            const int n = n0 + SW * c - 1;
+            if (E.form != kHGBat && E.form != kGriewank && n >= E.s1 && n + 1 < E.s2) {
+                const float u = ed.x - zl * zl;
+                const float v = zl - 1.f;
+                a += 100.f * u * u + v * v;
+            }
+            zl = ed.y;
+        }
+        const size_t o = (size_t)row * R.ntiles + blockIdx.x;
+        R.part[o] = make_float2(a, b);
+        R.zedge[o] = make_float2(s_edge[0][rt].x, zl);   // z at n0 and at the tile's last column
     }
     asm volatile("tcgen05.fence::before_thread_sync;" : : : "memory");
     __syncthreads();
@@ -881,6 +956,12 @@ apo_status big_run_group(const std::vector<BigSpec>& specs, cudaStream_t st, cha
     const size_t rank_smem = (size_t)max_chunk * kSortChunk * 8;
     if (e == cudaSuccess && rank_smem > 48 * 1024)
         e = cudaFuncSetAttribute(big_rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rank_smem);
+    // generation: four rows of Dp floats per warp
+    int max_dp = 4;
+    for (const BigRun& R : runs) max_dp = std::max(max_dp, R.Dp);
+    const size_t gen_smem = (size_t)kGenWarps * 4 * max_dp * 4;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(big_gen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gen_smem);
     StageTimer timer(st);
     auto gemm = [&]() -> cudaError_t {
         return timer.run(kStageGemm, [&] {
@@ -934,7 +1015,7 @@ apo_status big_run_group(const std::vector<BigSpec>& specs, cudaStream_t st, cha
                 e = rank(t);
                 if (e == cudaSuccess)
                     e = timer.run(kStageGen, [&] {
-                        big_gen_kernel<<<g_rows, 256, 0, st>>>(d_runs, t);
+                        big_gen_kernel<<<g_rows, 256, gen_smem, st>>>(d_runs, t);
                         return cudaGetLastError();
                     });
                 if (e == cudaSuccess) e = gemm();

@@ -238,7 +238,8 @@ __device__ __forceinline__ float hgbat_from_sums(float a, float c, int D)
 }
 
 // HGBat or Griewank (the forms that are not sums of per-coordinate terms) of
-// one row by one warp (z[d * zs]); Griewank uses y = 6 z and ew[d] = 1 / sqrt(d + 1).
+// one row by one warp (z[d * zs]); Griewank uses y = 6 z and ew[d] = 1 / (pi
+// sqrt(d + 1)), so that cos(y / sqrt(d + 1)) = cospi(y ew[d]).
 __device__ __forceinline__ float form2_value(const float* z, int zs, const DevComp& C, const float* ew, int D)
 {
     const int lane = threadIdx.x & 31;
@@ -255,7 +256,7 @@ __device__ __forceinline__ float form2_value(const float* z, int zs, const DevCo
     for (int d = lane; d < D; d += 32) {
         const float y = 6.f * z[(size_t)d * zs];
         s = fmaf(y, y, s);
-        p *= cosf(y * ew[d]);
+        p *= cospif(y * ew[d]);
     }
     return fmaf(warp_sum(s), 1.f / 4000.f, 1.f - warp_prod(p));
 }
