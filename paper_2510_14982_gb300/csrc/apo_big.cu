@@ -255,8 +255,9 @@ __global__ void __launch_bounds__(256, 1) big_gen_kernel(const BigRun* __restric
         uint4 w = make_uint4(0u, 0u, 0u, 0u);
         if (2 * q < D) w = philox((uint32_t)t, (uint32_t)r, (uint32_t)q, kSlotDim, seed, run);
         const bool v0 = 2 * q < D, v1 = 2 * q + 1 < D;
-        A[2 * j] = w.x; B[2 * j] = v0 ? w.y : 0u;
-        A[2 * j + 1] = w.z; B[2 * j + 1] = v1 ? w.w : 0u;
+        // slots past D get the key 2^32 - 1, which no threshold counts
+        A[2 * j] = w.x; B[2 * j] = v0 ? w.y : 0xFFFFFFFFu;
+        A[2 * j + 1] = w.z; B[2 * j + 1] = v1 ? w.w : 0xFFFFFFFFu;
         valid |= (v0 ? 1u : 0u) << (2 * j);
         valid |= (v1 ? 1u : 0u) << (2 * j + 1);
     }

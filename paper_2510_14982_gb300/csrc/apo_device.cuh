@@ -328,31 +328,38 @@ __device__ uint32_t warp_kselect(const uint32_t (&key)[2 * QPL], uint32_t valid,
     return sel;
 }
 
-// floor((2^32 - 1) / b) for b = 1 .. 2 (256 + 1): fixed-point reciprocals of
-// the interpolation denominators (slot 0 unused)
+// floor((2^32 - 1) / b) for b = 1 .. 2 (kBigMaxDim + 1): fixed-point
+// reciprocals of the interpolation denominators b = 2 (chi - clo + 1) <= 2 (n + 1)
+// (slot 0 unused)
+constexpr int kRecipSize = 2 * (kBigMaxDim + 1) + 1;
 struct RecipTable {
-    uint32_t v[516];
+    uint32_t v[kRecipSize];
 };
 constexpr RecipTable make_recip_table()
 {
     RecipTable t{};
-    for (int b = 1; b < 516; ++b) t.v[b] = (uint32_t)(0xFFFFFFFFull / (unsigned long long)b);
+    for (int b = 1; b < kRecipSize; ++b) t.v[b] = (uint32_t)(0xFFFFFFFFull / (unsigned long long)b);
     return t;
 }
 static __constant__ RecipTable kRecip = make_recip_table();
 
-// The same subset as warp_kselect, found by interpolation: a threshold T with
-// exactly k valid keys below it selects the k smallest (every key below T is
-// smaller than every key at or above it, so index tie-breaks cannot arise).
-// The keys are uniform 32-bit Philox words, so interpolating between the
-// bracketing counts usually lands between the k-th and (k+1)-th smallest key
-// within a few warp-wide counts (about 3.2 on average for D in 10..200 in
-// simulation; 3.5 measured in runs at D 100, ps 4096).  A boundary tie, or
-// no hit within ten counts (0.3 to 0.6% of selections), falls back to the
-// bitwise descent.  n = number of valid slots (<= 256).
+// The same subset as warp_kselect, found by interpolation and finished by
+// extremes: a threshold T with exactly k valid keys below it selects the k
+// smallest (every key below T is smaller than every key at or above it, so
+// index tie-breaks cannot arise).  The keys are uniform 32-bit Philox words,
+// so interpolating between the bracketing counts lands within a few keys of
+// k at the first count (the count is binomial around k).  Once the count c
+// at a threshold is within kAdjust of k, the set below it is corrected by c -
+// k warp-wide maximum reductions (each drops the largest selected key) or k -
+// c minimum reductions (each adds the smallest unselected key), instead of
+// further counts; a final count confirms exactly k keys (equal keys at the
+// boundary would give another count and take the exact bitwise descent, as
+// does no convergence within ten counts).  n = number of valid slots (<= 1024);
+// slots outside `valid` must hold the key 2^32 - 1, which no threshold counts.
 template <int QPL>
 __device__ uint32_t warp_kselect_interp(const uint32_t (&key)[2 * QPL], uint32_t valid, int k, int n)
 {
+    constexpr int kAdjust = 8;
     if (k <= 0) return 0;
     if (k >= n) return valid;
     // invariant: clo = #(keys < lo) < k < chi = #(keys <= hm); thresholds are
@@ -372,10 +379,42 @@ __device__ uint32_t warp_kselect_interp(const uint32_t (&key)[2 * QPL], uint32_t
         const uint32_t T = lo + off;
         uint32_t below = 0;
 #pragma unroll
-        for (int e = 0; e < 2 * QPL; ++e)
-            if (((valid >> e) & 1u) && key[e] < T) below |= 1u << e;
+        for (int e = 0; e < 2 * QPL; ++e) below |= (key[e] < T ? 1u : 0u) << e;
         const int c = __reduce_add_sync(0xffffffffu, __popc(below));
         if (c == k) return below;
+        if (c - k <= kAdjust && k - c <= kAdjust) {
+            uint32_t sel = below;
+            if (c > k) {
+                // drop the c - k largest selected keys
+                for (int i = 0; i < c - k; ++i) {
+                    uint32_t m = 0u;
+#pragma unroll
+                    for (int e = 0; e < 2 * QPL; ++e)
+                        if ((sel >> e) & 1u) m = max(m, key[e]);
+                    m = __reduce_max_sync(0xffffffffu, m);
+#pragma unroll
+                    for (int e = 0; e < 2 * QPL; ++e)
+                        if (((sel >> e) & 1u) && key[e] == m) sel &= ~(1u << e);
+                }
+            } else {
+                // add the k - c smallest unselected keys
+                const uint32_t rest = valid & ~below;
+                uint32_t cand = rest;
+                for (int i = 0; i < k - c; ++i) {
+                    uint32_t m = 0xFFFFFFFFu;
+#pragma unroll
+                    for (int e = 0; e < 2 * QPL; ++e)
+                        if ((cand >> e) & 1u) m = min(m, key[e]);
+                    m = __reduce_min_sync(0xffffffffu, m);
+#pragma unroll
+                    for (int e = 0; e < 2 * QPL; ++e)
+                        if (((cand >> e) & 1u) && key[e] == m) cand &= ~(1u << e);
+                }
+                sel = below | (rest & ~cand);
+            }
+            if (__reduce_add_sync(0xffffffffu, __popc(sel)) == k) return sel;
+            break;   // equal keys at the boundary
+        }
         if (c < k) { lo = T; clo = c; }
         else { hm = T - 1u; chi = c; }
     }

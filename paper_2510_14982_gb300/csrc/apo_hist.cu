@@ -1,78 +1,117 @@
 // apo_hist.cu -- 256-bin histograms of 8-bit images and the Otsu prefix
 // tables (the thresholding application of the cuAPO paper, Sec. 5.2).
 //
-// The histogram is HBM-bound: every pixel byte is read once with 16-byte
-// vector loads and counted into per-warp shared-memory sub-histograms, which
-// are merged into the image's global int32 bins with one atomic per bin and
-// CTA.  Integer counting makes the result independent of the order of
-// accumulation (bit-exact).
+// The histogram is HBM-bound in principle: every pixel byte is read once.
+// Shared-memory atomics (even with per-warp copies) cap it near a third of
+// the HBM rate on images whose intensities concentrate, so the counting is
+// atomic-free: every thread owns one 8-bit counter per bin, incremented with
+// a plain shared-memory byte load, add and store.  The counters are laid out
+// [bin][64 words], thread (warp w, lane l) owning byte w mod 4 of word l + 32
+// (w / 4) of every bin, so the 32 lanes of a warp always touch 32 different
+// banks whatever their pixel values.  Before any counter can overflow (at most
+// 240 pixels per thread between flushes) the CTA flushes: thread b sums the
+// 256 counters of bin b into its own 32-bit register total and clears them.
+// The totals go to the image's global int32 bins with one atomic per bin and
+// CTA.  Integer counting makes the result independent of the order (bit-exact).
 #include "apo_internal.h"
 
 namespace apo {
 
 constexpr int kHistThreads = 256;
-constexpr int kHistWarps = kHistThreads / 32;
-constexpr int kHistCopies = 4;                 // sub-histograms per warp (lane & 3)
-constexpr int kHistStride = 257;               // one pad word: copies sit on shifted banks
+constexpr int kHistWords = 64;          // counter words per bin (256 threads x 1 byte)
+constexpr int kHistRound = 15;          // 16-byte loads per thread between flushes (240 pixels < 256)
+constexpr int kHistBatch = 5;           // loads in flight per thread
+
+// byte offset of thread (warp, lane)'s counter of bin 0; bin b adds 256 b
+__device__ __forceinline__ int hist_slot(int warp, int lane)
+{
+    return 4 * (lane + 32 * (warp >> 2)) + (warp & 3);
+}
+
+// adds the 256 counters of bin `bin` (thread = bin) to total and clears them;
+// word i of the bin is read at step (i + bin) mod 64, so a warp's lanes read
+// 32 different banks
+__device__ __forceinline__ void hist_flush(unsigned char* cnt, int bin, unsigned& total)
+{
+    uint32_t* w = reinterpret_cast<uint32_t*>(cnt) + bin * kHistWords;
+    uint32_t lo = 0, hi = 0;   // four 16-bit lanes: at most 64 x 255 < 2^16 each
+#pragma unroll 8
+    for (int i = 0; i < kHistWords; ++i) {
+        const int k = (i + bin) & (kHistWords - 1);
+        const uint32_t v = w[k];
+        w[k] = 0u;
+        lo += v & 0x00FF00FFu;
+        hi += (v >> 8) & 0x00FF00FFu;
+    }
+    total += (lo & 0xFFFFu) + (lo >> 16) + (hi & 0xFFFFu) + (hi >> 16);
+}
 
 __global__ void __launch_bounds__(kHistThreads) histogram_u8_kernel(const uint8_t* __restrict__ px,
                                                                     long long n_per_image,
                                                                     long long chunk, int32_t* hist)
 {
-    // Equal pixel values within a warp serialise shared-memory atomics; four
-    // copies per warp (lanes split by lane & 3) cut those collisions.
-    __shared__ unsigned sub[kHistWarps * kHistCopies * kHistStride];
+    extern __shared__ __align__(16) unsigned char cnt[];   // 256 * kHistWords * 4 = 64 KB
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < kHistWarps * kHistCopies * kHistStride; i += kHistThreads) sub[i] = 0;
+    for (int i = tid; i < 256 * kHistWords; i += kHistThreads) reinterpret_cast<uint32_t*>(cnt)[i] = 0u;
     __syncthreads();
+    unsigned char* my = cnt + hist_slot(warp, lane);
+    unsigned total = 0;   // this thread's bin (tid) over the flushes
 
     const int image = blockIdx.y;
     const long long begin = (long long)blockIdx.x * chunk;
     long long end = begin + chunk;
     if (end > n_per_image) end = n_per_image;
     const uint8_t* base = px + (size_t)image * (size_t)n_per_image;
-    unsigned* h = sub + (warp * kHistCopies + (lane & (kHistCopies - 1))) * kHistStride;
+    auto count = [&](uint32_t word) {
+        my[256 * (word & 255u)] += 1;
+        my[256 * ((word >> 8) & 255u)] += 1;
+        my[256 * ((word >> 16) & 255u)] += 1;
+        my[256 * (word >> 24)] += 1;
+    };
 
-    // bytes before the first 16-byte boundary and after the last one
+    // bytes before the first 16-byte boundary and after the last one (fewer
+    // than 16 + 15 per CTA: one per thread at most)
     const uintptr_t addr = reinterpret_cast<uintptr_t>(base + begin);
     long long head = (long long)((16 - (addr & 15)) & 15);
     if (head > end - begin) head = end - begin;
-    for (long long i = begin + tid; i < begin + head; i += kHistThreads) atomicAdd(&h[base[i]], 1u);
     const long long vbeg = begin + head;
     const long long nvec = (end - vbeg) >> 4;
+    const long long tail0 = vbeg + (nvec << 4);
+    if (tid < head) my[256 * base[begin + tid]] += 1;
+    if (tid < end - tail0) my[256 * base[tail0 + tid]] += 1;
+
     const uint4* v = reinterpret_cast<const uint4*>(base + vbeg);
-    long long i = tid;
-    for (; i + kHistThreads < nvec; i += 2 * kHistThreads) {   // two 16-byte loads in flight
-        const uint4 w0 = __ldcs(v + i);
-        const uint4 w1 = __ldcs(v + i + kHistThreads);
-        const uint32_t words[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    const long long per_round = (long long)kHistRound * kHistThreads;
+    for (long long r0 = 0; r0 < nvec; r0 += per_round) {
+        // one round: at most kHistRound loads (4 kHistRound + 2 bytes) per thread
+#pragma unroll 1
+        for (int b0 = 0; b0 < kHistRound; b0 += kHistBatch) {
+            uint4 w[kHistBatch];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            atomicAdd(&h[words[k] & 255u], 1u);
-            atomicAdd(&h[(words[k] >> 8) & 255u], 1u);
-            atomicAdd(&h[(words[k] >> 16) & 255u], 1u);
-            atomicAdd(&h[words[k] >> 24], 1u);
+            for (int k = 0; k < kHistBatch; ++k) {
+                const long long i = r0 + (long long)(b0 + k) * kHistThreads + tid;
+                w[k] = i < nvec ? __ldcs(v + i) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int k = 0; k < kHistBatch; ++k) {
+                const long long i = r0 + (long long)(b0 + k) * kHistThreads + tid;
+                if (i < nvec) {
+                    count(w[k].x);
+                    count(w[k].y);
+                    count(w[k].z);
+                    count(w[k].w);
+                }
+            }
         }
+        __syncthreads();
+        hist_flush(cnt, tid, total);
+        __syncthreads();
     }
-    for (; i < nvec; i += kHistThreads) {
-        const uint4 w = __ldcs(v + i);
-        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            atomicAdd(&h[words[k] & 255u], 1u);
-            atomicAdd(&h[(words[k] >> 8) & 255u], 1u);
-            atomicAdd(&h[(words[k] >> 16) & 255u], 1u);
-            atomicAdd(&h[words[k] >> 24], 1u);
-        }
+    if (nvec == 0) {   // the head / tail bytes only
+        __syncthreads();
+        hist_flush(cnt, tid, total);
     }
-    for (long long j = vbeg + (nvec << 4) + tid; j < end; j += kHistThreads) atomicAdd(&h[base[j]], 1u);
-    __syncthreads();
-    for (int b = tid; b < 256; b += kHistThreads) {
-        unsigned s = 0;
-#pragma unroll
-        for (int c = 0; c < kHistWarps * kHistCopies; ++c) s += sub[c * kHistStride + b];
-        if (s) atomicAdd(reinterpret_cast<unsigned*>(hist + (size_t)image * 256 + b), s);
-    }
+    if (total) atomicAdd(reinterpret_cast<unsigned*>(hist + (size_t)image * 256 + tid), total);
 }
 
 cudaError_t launch_histogram_u8(const uint8_t* d_px, int64_t n_per_image, int n_images, int32_t* d_hist,
@@ -83,14 +122,18 @@ cudaError_t launch_histogram_u8(const uint8_t* d_px, int64_t n_per_image, int n_
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // about eight CTAs per SM over the whole batch, each a 16-byte multiple
+    // about three CTAs per SM at a time (64 KB of counters each), a few waves
+    // over the whole batch, each chunk a 16-byte multiple
     long long total = n_per_image * (long long)n_images;
-    long long chunk = total / ((long long)sms * 8);
+    long long chunk = total / ((long long)sms * 12);
     if (chunk < 65536) chunk = 65536;
     chunk = (chunk + 15) & ~15ll;
     long long per_image = (n_per_image + chunk - 1) / chunk;
     dim3 grid((unsigned)per_image, (unsigned)n_images);
-    histogram_u8_kernel<<<grid, kHistThreads, 0, st>>>(d_px, n_per_image, chunk, d_hist);
+    const int smem = 256 * kHistWords * 4;
+    e = cudaFuncSetAttribute(histogram_u8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    histogram_u8_kernel<<<grid, kHistThreads, smem, st>>>(d_px, n_per_image, chunk, d_hist);
     return cudaGetLastError();
 }
 

@@ -638,8 +638,9 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
         if (j == QPL - 1 && merged) w = jw;   // lanes >= jb hold no pair here (2 q >= D)
         else w = philox((uint32_t)t, (uint32_t)r, (uint32_t)q, kSlotDim | cs, seed, run);
         const bool v0 = 2 * q < D, v1 = 2 * q + 1 < D;
-        A[2 * j] = v0 ? w.x : 0u; B[2 * j] = v0 ? w.y : 0u;
-        A[2 * j + 1] = v0 ? w.z : 0u; B[2 * j + 1] = v0 ? w.w : 0u;
+        // slots past D get the key 2^32 - 1, which no threshold counts
+        A[2 * j] = v0 ? w.x : 0u; B[2 * j] = v0 ? w.y : 0xFFFFFFFFu;
+        A[2 * j + 1] = v0 ? w.z : 0u; B[2 * j + 1] = v1 ? w.w : 0xFFFFFFFFu;
         valid |= (v0 ? 1u : 0u) << (2 * j);
         valid |= (v1 ? 1u : 0u) << (2 * j + 1);
     }
