@@ -197,6 +197,11 @@ typedef struct apo_batch_options {
                              Runs whose population fits stay resident in shared memory,
                              the others keep it in global memory.                     */
     int ctas_per_sm;      /* work-queue CTAs per SM; 0 = as many as fit                */
+    int cluster_ps;       /* 0: every run of ps <= 1024 takes one work-queue CTA.  > 0:
+                             runs with cluster_ps <= ps <= 1024 take one thread-block
+                             cluster of cluster_size CTAs each instead (the multi-CTA
+                             iteration loop, its CTAs co-scheduled by the hardware)  */
+    int cluster_size;     /* 2..8 when cluster_ps > 0                                */
 } apo_batch_options;
 
 apo_status apo_batch_create(const apo_problem* const* probs, const apo_params* params, int n_runs,
@@ -205,9 +210,11 @@ apo_status apo_batch_create(const apo_problem* const* probs, const apo_params* p
 apo_status apo_batch_launch(apo_batch* batch, void* stream);
 
 /* Autotuner: times the batch, truncated to its first `probe_iters`
- * iterations, under candidate work-queue configurations (shared-memory
- * budgets for 1, 2, 3 and 4 CTAs per SM), keeps the fastest and re-plans the
- * batch with it.  Writes the choice to *chosen when not NULL.  Synchronous. */
+ * iterations, under candidate configurations -- the work-queue shared-memory
+ * budget for 1, 2, 3 and 4 CTAs per SM, each with one CTA per run or with the
+ * larger runs on one cluster per run (ps >= 256 on 2 or 4 CTAs, ps >= 384 on
+ * 4) -- keeps the fastest and re-plans the batch with it.  Writes the choice
+ * to *chosen when not NULL.  Synchronous. */
 apo_status apo_batch_autotune(apo_batch* batch, void* stream, int probe_iters, apo_batch_options* chosen);
 void apo_batch_destroy(apo_batch* batch);
 

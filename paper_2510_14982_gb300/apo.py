@@ -52,7 +52,8 @@ class apo_params(C.Structure):
 
 
 class apo_batch_options(C.Structure):
-    _fields_ = [("smem_budget", C.c_size_t), ("ctas_per_sm", C.c_int)]
+    _fields_ = [("smem_budget", C.c_size_t), ("ctas_per_sm", C.c_int), ("cluster_ps", C.c_int),
+                ("cluster_size", C.c_int)]
 
 
 class apo_surrogate_params(C.Structure):
@@ -285,7 +286,8 @@ class Batch:
         o = apo_batch_options()
         _check(_lib.apo_batch_autotune(self.handle, _stream(stream), int(probe_iters), C.byref(o)),
                "apo_batch_autotune")
-        return {"smem_budget": int(o.smem_budget), "ctas_per_sm": int(o.ctas_per_sm)}
+        return {"smem_budget": int(o.smem_budget), "ctas_per_sm": int(o.ctas_per_sm),
+                "cluster_ps": int(o.cluster_ps), "cluster_size": int(o.cluster_size)}
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -295,11 +297,11 @@ class Batch:
 
 
 def apo_batch_create(probs, params, d_best_x, x_stride, d_best_f, d_curves=None, curve_stride=0,
-                     smem_budget=0, ctas_per_sm=0) -> Batch:
+                     smem_budget=0, ctas_per_sm=0, cluster_ps=0, cluster_size=0) -> Batch:
     n = len(probs)
     handles = (_P * n)(*[p.handle for p in probs])
     prm = (apo_params * n)(*params)
-    opt = apo_batch_options(int(smem_budget), int(ctas_per_sm))
+    opt = apo_batch_options(int(smem_budget), int(ctas_per_sm), int(cluster_ps), int(cluster_size))
     h = _P()
     _check(_lib.apo_batch_create(handles, prm, n, _dptr(d_best_x), int(x_stride), _dptr(d_best_f), _dptr(d_curves),
                                  int(curve_stride), C.byref(opt), C.byref(h)), "apo_batch_create")

@@ -575,6 +575,7 @@ struct LaunchInfo {
     bool grid, fit64;
     int qpl, g, ctas;
     size_t smem;
+    bool cluster;       // grid kernel with one thread-block cluster of g CTAs per run
 };
 
 // Everything a set of runs needs on the device, planned and uploaded once;
@@ -600,7 +601,8 @@ void release_prepared(Prepared& PR, cudaStream_t st);
 // their layout fits `queue_budget` bytes.  queue_ctas_per_sm limits the
 // persistent work-queue grid (0 = occupancy limit).
 apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, bool async_alloc,
-                        size_t queue_budget, int queue_ctas_per_sm, Prepared* out)
+                        size_t queue_budget, int queue_ctas_per_sm, Prepared* out, int cluster_ps = 0,
+                        int cluster_size = 0)
 {
     Prepared& PR = *out;
     const int n = (int)specs_in.size();
@@ -612,7 +614,7 @@ apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, b
     if (queue_budget == 0 || queue_budget > kSmemMax) queue_budget = kSmemMax;
 
     // per-run layout and kernel class
-    struct Cls { bool grid, fit64; int qpl; };
+    struct Cls { bool grid, fit64; int qpl; bool cluster; };
     std::vector<SmemPlan> plans(n);
     std::vector<Cls> cls(n);
     for (int k = 0; k < n; ++k) {
@@ -623,9 +625,12 @@ apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, b
             set_err("prepared batches support D <= %d (run D = %d with apo_run_batch)", kSmallMaxDim, s.P->D);
             return APO_ERR_UNSUPPORTED;
         }
-        // a lone run of a large population spreads over many CTAs
-        const bool grid = ps > kQueueMaxPs || (n == 1 && ps >= kGridSingleMinPs);
-        cls[k] = {grid, f64, f64 ? 1 : qpl_of(s.P)};
+        // a lone run of a large population spreads over many CTAs; runs of
+        // at least cluster_ps protozoa in a batch take a cluster of
+        // cluster_size CTAs each (the grid kernel, launched as clusters)
+        const bool big_pop = ps > kQueueMaxPs || (n == 1 && ps >= kGridSingleMinPs);
+        const bool cl = !big_pop && cluster_ps > 0 && cluster_size >= 2 && ps >= cluster_ps;
+        cls[k] = {big_pop || cl, f64, f64 ? 1 : qpl_of(s.P), cl};
         if (cls[k].grid) {
             plans[k] = choose_plan(s.P, ps, false, true, kSmemMax);
         } else {
@@ -635,8 +640,9 @@ apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, b
         if (plans[k].total > kSmemMax) { set_err("problem needs too much shared memory (ps %d)", ps); return APO_ERR_UNSUPPORTED; }
     }
     // launch groups: one per kernel class; work-queue runs longest first
-    std::map<std::tuple<int, int, int>, std::vector<int>> groups;
-    for (int k = 0; k < n; ++k) groups[std::make_tuple((int)cls[k].grid, (int)cls[k].fit64, cls[k].qpl)].push_back(k);
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
+    for (int k = 0; k < n; ++k)
+        groups[std::make_tuple((int)cls[k].grid, (int)cls[k].cluster, (int)cls[k].fit64, cls[k].qpl)].push_back(k);
     std::vector<int> order;
     for (auto& kv : groups) {
         std::vector<int>& v = kv.second;
@@ -652,9 +658,22 @@ apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, b
             int cap = run_kernel_capacity(c.fit64, c.qpl, smem, false);
             if (cap <= 0) { set_err("work-queue kernel cannot be resident with %zu B of shared memory", smem); return APO_ERR_UNSUPPORTED; }
             if (queue_ctas_per_sm > 0) cap = std::min(cap, queue_ctas_per_sm * sms);
-            PR.launches.push_back({(int)order.size(), (int)v.size(), false, c.fit64, c.qpl, 1, std::min(cap, (int)v.size()), smem});
+            PR.launches.push_back({(int)order.size(), (int)v.size(), false, c.fit64, c.qpl, 1, std::min(cap, (int)v.size()), smem,
+                                   false});
             order.insert(order.end(), v.begin(), v.end());
             PR.queue_smem_cap = std::max(PR.queue_smem_cap, smem);
+            continue;
+        }
+        if (c.cluster) {
+            // longest first, as in the work queue: clusters are scheduled in order
+            auto cost = [&](int k) {
+                const double D = specs_in[k].P->D;
+                return (double)specs_in[k].prm.ps * (D * D + 40.0 * D) * (specs_in[k].t_end - specs_in[k].t_begin + 1);
+            };
+            std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return cost(a) > cost(b); });
+            PR.launches.push_back({(int)order.size(), (int)v.size(), true, c.fit64, c.qpl, cluster_size,
+                                   (int)v.size() * cluster_size, smem, true});
+            order.insert(order.end(), v.begin(), v.end());
             continue;
         }
         const int cap = run_kernel_capacity(c.fit64, c.qpl, smem, true);
@@ -666,7 +685,7 @@ apo_status prepare_runs(const std::vector<RunSpec>& specs_in, cudaStream_t st, b
                 const int want = (specs_in[v[i + j]].prm.ps + kGridMinRows - 1) / kGridMinRows;
                 g = std::max(1, std::min(g, want));
             }
-            PR.launches.push_back({(int)order.size(), cnt, true, c.fit64, c.qpl, g, cnt * g, smem});
+            PR.launches.push_back({(int)order.size(), cnt, true, c.fit64, c.qpl, g, cnt * g, smem, false});
             order.insert(order.end(), v.begin() + i, v.begin() + i + cnt);
         }
     }
@@ -805,7 +824,7 @@ apo_status launch_prepared(const Prepared& PR, cudaStream_t st)
     for (size_t l = 0; l < PR.launches.size() && e == cudaSuccess; ++l) {
         const LaunchInfo& L = PR.launches[l];
         e = launch_run(PR.d_runs + L.first, L.count, L.grid ? L.g : 0, L.ctas, PR.d_ctrl + l, status, L.smem,
-                       L.fit64, L.qpl, st);
+                       L.fit64, L.qpl, st, L.cluster);
     }
     if (e != cudaSuccess) { set_err("run launch failed: %s", cudaGetErrorString(e)); return APO_ERR_CUDA; }
     if (timed) APO_CUDA(cudaEventRecord(g_ev_after, st));
@@ -1012,7 +1031,15 @@ extern "C" apo_status apo_batch_create(const apo_problem* const* probs, const ap
     if (rc != APO_OK) { delete B; return rc; }
     B->opt.smem_budget = opt ? opt->smem_budget : 0;
     B->opt.ctas_per_sm = opt ? opt->ctas_per_sm : 0;
-    rc = prepare_runs(B->specs, 0, false, B->opt.smem_budget, B->opt.ctas_per_sm, &B->prep);
+    B->opt.cluster_ps = opt ? opt->cluster_ps : 0;
+    B->opt.cluster_size = opt ? opt->cluster_size : 0;
+    if (B->opt.cluster_ps < 0 || (B->opt.cluster_ps > 0 && (B->opt.cluster_size < 2 || B->opt.cluster_size > 8))) {
+        delete B;
+        set_err("cluster_size must be 2..8 when cluster_ps > 0");
+        return APO_ERR_INVALID_ARG;
+    }
+    rc = prepare_runs(B->specs, 0, false, B->opt.smem_budget, B->opt.ctas_per_sm, &B->prep, B->opt.cluster_ps,
+                      B->opt.cluster_size);
     if (rc != APO_OK) { delete B; return rc; }
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1041,15 +1068,21 @@ extern "C" apo_status apo_batch_autotune(apo_batch* B, void* stream, int probe_i
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::vector<RunSpec> probe = B->specs;
     for (RunSpec& s : probe) s.t_end = std::min(s.t_end, probe_iters);
+    // candidates: the work-queue budget for 1 to 4 CTAs per SM, each with
+    // every run in the work queue (one CTA per run) or with the larger runs
+    // on one cluster of 2 or 4 CTAs each
     const size_t budgets[4] = {kSmemMax, 113 * 1024, 75 * 1024, 56 * 1024};
+    const int clusters[4][2] = {{0, 0}, {256, 2}, {256, 4}, {384, 4}};
     cudaEvent_t e0, e1;
     APO_CUDA(cudaEventCreate(&e0));
     APO_CUDA(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     apo_batch_options best = B->opt;
-    for (size_t c = 0; c < 4; ++c) {
+    for (size_t cand = 0; cand < 16; ++cand) {
+        const size_t c = cand / 4;
+        const int cps = clusters[cand % 4][0], csz = clusters[cand % 4][1];
         Prepared PR;
-        if (prepare_runs(probe, st, false, budgets[c], 0, &PR) != APO_OK) continue;
+        if (prepare_runs(probe, st, false, budgets[c], 0, &PR, cps, csz) != APO_OK) continue;
         float ms = 1e30f;
         bool ok = launch_prepared(PR, st) == APO_OK;   // warm-up
         for (int rep = 0; rep < 2 && ok; ++rep) {
@@ -1068,6 +1101,8 @@ extern "C" apo_status apo_batch_autotune(apo_batch* B, void* stream, int probe_i
             best_ms = ms;
             best.smem_budget = budgets[c];
             best.ctas_per_sm = 0;
+            best.cluster_ps = cps;
+            best.cluster_size = csz;
         }
     }
     cudaEventDestroy(e0);
@@ -1077,7 +1112,8 @@ extern "C" apo_status apo_batch_autotune(apo_batch* B, void* stream, int probe_i
     release_prepared(B->prep, st);
     B->prep = Prepared();
     B->opt = best;
-    apo_status rc = prepare_runs(B->specs, st, false, best.smem_budget, best.ctas_per_sm, &B->prep);
+    apo_status rc = prepare_runs(B->specs, st, false, best.smem_budget, best.ctas_per_sm, &B->prep, best.cluster_ps,
+                                 best.cluster_size);
     if (rc != APO_OK) return rc;
     if (chosen) *chosen = best;
     return APO_OK;

@@ -29,12 +29,14 @@ cudaError_t launch_dr(const ApoRun* d_runs, const int* d_offs, int n_runs, int n
 
 // Launches the APO iteration loop.  grid_g > 0: cooperative launch of
 // n_runs * grid_g CTAs of the grid kernel (512 threads), CTA b serving run
-// b / grid_g.  grid_g == 0: a persistent work-queue launch of n_ctas CTAs
-// (256 threads) popping runs from *d_queue.
-// fit64 selects float64 fitness (Otsu); qpl is the dimension-pair count per
-// lane (1, 2 or 4).
+// b / grid_g; with cluster, a plain launch in which the grid_g CTAs of each
+// run form one thread-block cluster (grid_g <= 8).  grid_g == 0: a
+// persistent work-queue launch of n_ctas CTAs (256 threads) popping runs
+// from *d_queue.  fit64 selects float64 fitness (Otsu); qpl is the
+// dimension-pair count per lane (1, 2 or 4).
 cudaError_t launch_run(const ApoRun* d_runs, int n_runs, int grid_g, int n_ctas, int* d_queue,
-                       int* d_status, size_t smem_bytes, bool fit64, int qpl, cudaStream_t st);
+                       int* d_status, size_t smem_bytes, bool fit64, int qpl, cudaStream_t st,
+                       bool cluster = false);
 
 // Largest number of co-resident CTAs of the work-queue kernel (grid = false)
 // or of the cooperative grid kernel (grid = true) for this shared-memory size

@@ -780,8 +780,30 @@ cudaError_t launch_dr(const ApoRun* d_runs, const int* d_offs, int n_runs, int n
 
 template <typename FitT, int QPL>
 static cudaError_t launch_run_t(const ApoRun* d_runs, int n_runs, int grid_g, int n_ctas, int* d_queue,
-                                int* d_status, size_t smem, cudaStream_t st)
+                                int* d_status, size_t smem, bool cluster, cudaStream_t st)
 {
+    if (grid_g > 0 && cluster) {
+        // cluster per run: the g CTAs of a run form one thread-block cluster,
+        // which the hardware co-schedules, so their barriers always complete;
+        // runs need not be co-resident with one another, and clusters are
+        // scheduled as SMs free up
+        auto fn = grid_kernel<FitT, QPL>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(n_runs * grid_g);
+        cfg.blockDim = dim3(kGridThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)grid_g;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, fn, d_runs, n_runs, grid_g, d_status);
+    }
     if (grid_g > 0) {
         auto fn = grid_kernel<FitT, QPL>;
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -798,16 +820,17 @@ static cudaError_t launch_run_t(const ApoRun* d_runs, int n_runs, int grid_g, in
 }
 
 cudaError_t launch_run(const ApoRun* d_runs, int n_runs, int grid_g, int n_ctas, int* d_queue, int* d_status,
-                       size_t smem, bool fit64, int qpl, cudaStream_t st)
+                       size_t smem, bool fit64, int qpl, cudaStream_t st, bool cluster)
 {
     if (fit64) {
-        if (qpl == 1) return launch_run_t<double, 1>(d_runs, n_runs, grid_g, n_ctas, d_queue, d_status, smem, st);
+        if (qpl == 1)
+            return launch_run_t<double, 1>(d_runs, n_runs, grid_g, n_ctas, d_queue, d_status, smem, cluster, st);
         return cudaErrorInvalidValue;
     }
     switch (qpl) {
-    case 1: return launch_run_t<float, 1>(d_runs, n_runs, grid_g, n_ctas, d_queue, d_status, smem, st);
-    case 2: return launch_run_t<float, 2>(d_runs, n_runs, grid_g, n_ctas, d_queue, d_status, smem, st);
-    case 4: return launch_run_t<float, 4>(d_runs, n_runs, grid_g, n_ctas, d_queue, d_status, smem, st);
+    case 1: return launch_run_t<float, 1>(d_runs, n_runs, grid_g, n_ctas, d_queue, d_status, smem, cluster, st);
+    case 2: return launch_run_t<float, 2>(d_runs, n_runs, grid_g, n_ctas, d_queue, d_status, smem, cluster, st);
+    case 4: return launch_run_t<float, 4>(d_runs, n_runs, grid_g, n_ctas, d_queue, d_status, smem, cluster, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -281,3 +281,35 @@ def test_single_threshold_at_the_papers_settings(apo, orc, side):
     bx, bf, _ = apo.apo_run(prob, apo.apo_params_make(100, 1, 0.1, 50, side))
     best = max(orc.otsu_sigma_b2(hist, np.array([t])) for t in range(256))
     assert -bf == best
+
+
+@pytest.mark.parametrize("cluster_ps,cluster_size", [(100, 2), (200, 4), (20, 8)])
+def test_cluster_per_run_mapping_equals_work_queue(apo, cluster_ps, cluster_size):
+    """Runs mapped to one thread-block cluster each (the multi-CTA iteration
+    loop, its CTAs co-scheduled by the hardware) give the work queue's results
+    bit for bit, directly and replayed from a CUDA graph."""
+    import torch
+    runs = inputs.batched_runs(n_runs=20, seed=4)
+    T = 30
+    probs = [apo.problem_from_spec(s) for s, _ in runs]
+    prms = [apo.apo_params_make(ps, 1, 0.1, T, 8, k) for k, (_, ps) in enumerate(runs)]
+    n = len(runs)
+    ref_x = torch.zeros((n, 50), device="cuda")
+    ref_f = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ref_c = torch.zeros((n, T + 1), device="cuda")
+    apo.apo_run_batch(probs, prms, ref_x, 50, ref_f, ref_c, T + 1)
+    torch.cuda.synchronize()
+    bx, bf, bc = torch.zeros_like(ref_x), torch.zeros_like(ref_f), torch.zeros_like(ref_c)
+    b = apo.apo_batch_create(probs, prms, bx, 50, bf, bc, T + 1, cluster_ps=cluster_ps, cluster_size=cluster_size)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.launch(s)
+    s.synchronize()
+    assert torch.equal(bf, ref_f) and torch.equal(bc, ref_c) and torch.equal(bx, ref_x)
+    bf.zero_(); bc.zero_(); bx.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.launch(s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(bf, ref_f) and torch.equal(bc, ref_c) and torch.equal(bx, ref_x)
