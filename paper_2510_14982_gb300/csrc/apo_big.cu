@@ -54,10 +54,14 @@ constexpr int kGenWarps = 8;
 constexpr int kBM = 128;                    // GEMM tile rows (candidates)
 constexpr int kBK = 64;                     // GEMM K block: 64 fp16 = 128 bytes
 constexpr int kSortChunk = 1024;            // keys per sorted chunk
-// 16 warps: warp 0 lane 0 issues the TMA loads, warp 1 lane 0 the MMAs; in
-// the epilogue warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its candidate
-// rows) and the column quarter w / 4 of the tile
-constexpr int kGemmThreads = 512;
+// The GEMM is persistent: one CTA per SM walks its share of the tiles.  Warp
+// kEpiWarps (lane 0) issues the TMA loads, warp kEpiWarps + 1 (lane 0) the
+// MMAs, and warps 0 .. kEpiWarps - 1 run the epilogue: warp w reads TMEM
+// lanes 32 (w mod 4) .. + 31 (its candidate rows) and the column quarter w / 4
+// of the tile.  The epilogue hands the accumulator back as soon as it has read
+// it, so a tile's objective terms are computed while the next tile's MMAs run.
+constexpr int kEpiWarps = 16;
+constexpr int kGemmThreads = 32 * (kEpiWarps + 2);
 constexpr int kGemmSmem = 192 * 1024;       // operand stages
 constexpr int kTileA = kBM * kBK * 2;       // bytes of one A part tile
 
@@ -403,7 +407,7 @@ struct EpiForm {
 };
 
 template <int W>
-__device__ __forceinline__ void epi_terms(const float (&z)[W], int n, const EpiForm& E, const float* ew_s, int n0,
+__device__ __forceinline__ void epi_terms(const float (&z)[W], int n, const EpiForm& E, const float* __restrict__ ew,
                                           float& s1, float& s2, float& prev, bool& have_prev)
 {
 #pragma unroll
@@ -418,9 +422,9 @@ __device__ __forceinline__ void epi_terms(const float (&z)[W], int n, const EpiF
         } else if (E.form == kGriewank) {
             const float y = 6.f * v;
             s1 = fmaf(y, y, s1);
-            s2 *= cospif(y * ew_s[c - n0]);   // ew = 1 / (pi sqrt(c + 1))
+            s2 *= cospif(y * __ldg(ew + c));   // ew = 1 / (pi sqrt(c + 1))
         } else if (c < E.s1) {
-            s1 = fmaf(ew_s[c - n0] * v, v, s1);
+            s1 = fmaf(__ldg(ew + c) * v, v, s1);
         } else if (c < E.s2) {
             if (have_prev && c - 1 >= E.s1) {
                 const float a = v - prev * prev;
@@ -435,47 +439,56 @@ __device__ __forceinline__ void epi_terms(const float (&z)[W], int n, const EpiF
     }
 }
 
+// Tile t of a launch (N tiles fastest, then M tiles, then runs): run, m0, n0;
+// false for tiles outside the run's population or dimension.
+struct TileGrid {
+    int max_mt, max_nt, BN;
+};
+
+__device__ __forceinline__ bool tile_of(int t, const TileGrid& G, const BigRun* runs, int& run, int& m0, int& n0)
+{
+    const int per_run = G.max_mt * G.max_nt;
+    run = t / per_run;
+    const int r = t - run * per_run;
+    m0 = (r / G.max_nt) * kBM;
+    n0 = (r % G.max_nt) * G.BN;
+    const BigRun& R = runs[run];
+    return m0 < R.ps && n0 < R.D;
+}
+
 template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1)
-    big_gemm_kernel(const BigRun* __restrict__ runs, const __grid_constant__ BigMaps maps)
+    big_gemm_kernel(const BigRun* __restrict__ runs, const __grid_constant__ BigMaps maps, TileGrid G, int n_tiles)
 {
     using Cfg = GemmCfg<BN>;
-    // N tiles vary fastest, so the CTAs that share an A tile run together and
-    // read it from L2 rather than HBM
-    const int run = blockIdx.z;
-    const BigRun& R = runs[run];
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
-    if (m0 >= R.ps || n0 >= R.D) return;
     extern __shared__ unsigned char gemm_dyn[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(gemm_dyn) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) unsigned long long full_bar[Cfg::kStages], empty_bar[Cfg::kStages], done_bar;
+    __shared__ __align__(8) unsigned long long full_bar[Cfg::kStages], empty_bar[Cfg::kStages];
+    __shared__ __align__(8) unsigned long long tfull_bar, tempty_bar, drain_bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ float ew_s[BN];
     __shared__ float2 s_quart[4][kBM], s_edge[4][kBM];
-    __shared__ int s_err;
+    __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = (R.D + kBK - 1) / kBK;
     const uint32_t sbase = smem_u32(smem);
+    auto aborted = [&]() { return *reinterpret_cast<volatile int*>(&s_abort) != 0; };
+    auto abort_all = [&](int* status) {
+        atomicExch(&s_abort, 1);
+        set_status(status, 4 /* APO_ERR_TIMEOUT */);
+    };
 
     if (threadIdx.x == 0) {
-        s_err = 0;
+        s_abort = 0;
         for (int s = 0; s < Cfg::kStages; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        mbar_init(smem_u32(&done_bar), 1);
+        mbar_init(smem_u32(&tfull_bar), 1);
+        mbar_init(smem_u32(&tempty_bar), kEpiWarps);
+        mbar_init(smem_u32(&drain_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" : : : "memory");
-        tma_prefetch_desc(&maps.yh[run]);
-        tma_prefetch_desc(&maps.yl[run]);
-        tma_prefetch_desc(&maps.gh[run]);
-        tma_prefetch_desc(&maps.gl[run]);
     }
-    for (int i = threadIdx.x; i < BN; i += blockDim.x) {
-        const int c = min(n0 + i, R.D - 1);
-        ew_s[i] = R.ew[c];
-    }
-    if (warp == 2) {
+    if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :
                      : "r"(smem_u32(&tmem_slot)), "r"(Cfg::kCols)
@@ -486,133 +499,187 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" : : : "memory");
     const uint32_t tmem = tmem_slot;
+    int* status = runs[0].status;
 
     auto stage_a_hi = [&](int s) { return sbase + (uint32_t)(s * Cfg::kStage); };
     auto stage_a_lo = [&](int s) { return sbase + (uint32_t)(s * Cfg::kStage + kTileA); };
     auto stage_b_hi = [&](int s) { return sbase + (uint32_t)(s * Cfg::kStage + 2 * kTileA); };
     auto stage_b_lo = [&](int s) { return sbase + (uint32_t)(s * Cfg::kStage + 2 * kTileA + Cfg::kTileB); };
 
-    int issued = 0;   // producer: K blocks whose loads were issued
-    if (warp == 0 && lane == 0) {
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % Cfg::kStages;
-            if (kb >= Cfg::kStages && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)((kb / Cfg::kStages - 1) & 1))) {
-                atomicExch(&s_err, 1);
-                break;
+    long long issued = 0;   // producer: K blocks whose loads were issued (all tiles)
+    if (warp == kEpiWarps) {
+        // ---- TMA producer
+        if (lane == 0) {
+            long long g = 0;
+            for (int t = blockIdx.x; t < n_tiles && !aborted(); t += gridDim.x) {
+                int run, m0, n0;
+                if (!tile_of(t, G, runs, run, m0, n0)) continue;
+                const int nk = (runs[run].D + kBK - 1) / kBK;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = (int)(g % Cfg::kStages);
+                    if (g >= Cfg::kStages &&
+                        !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)(((g / Cfg::kStages) - 1) & 1))) {
+                        abort_all(status);
+                        break;
+                    }
+                    if (aborted()) break;
+                    const uint32_t fb = smem_u32(&full_bar[s]);
+                    mbar_expect_tx(fb, (uint32_t)Cfg::kStage);
+                    const int k0 = kb * kBK;
+                    tma_load_2d(stage_a_hi(s), &maps.yh[run], k0, m0, fb);
+                    tma_load_2d(stage_a_lo(s), &maps.yl[run], k0, m0, fb);
+                    tma_load_2d(stage_b_hi(s), &maps.gh[run], k0, n0, fb);
+                    tma_load_2d(stage_b_lo(s), &maps.gl[run], k0, n0, fb);
+                    issued = g + 1;
+                }
             }
-            if (atomicAdd(&s_err, 0) != 0) break;
-            const uint32_t fb = smem_u32(&full_bar[s]);
-            mbar_expect_tx(fb, (uint32_t)Cfg::kStage);
-            const int k0 = kb * kBK;
-            tma_load_2d(stage_a_hi(s), &maps.yh[run], k0, m0, fb);
-            tma_load_2d(stage_a_lo(s), &maps.yl[run], k0, m0, fb);
-            tma_load_2d(stage_b_hi(s), &maps.gh[run], k0, n0, fb);
-            tma_load_2d(stage_b_lo(s), &maps.gl[run], k0, n0, fb);
-            ++issued;
         }
-    } else if (warp == 1 && lane == 0) {
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % Cfg::kStages;
-            if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((kb / Cfg::kStages) & 1))) {
-                atomicExch(&s_err, 1);
+    } else if (warp == kEpiWarps + 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            long long g = 0;
+            int it = 0;
+            for (int t = blockIdx.x; t < n_tiles && !aborted(); t += gridDim.x) {
+                int run, m0, n0;
+                if (!tile_of(t, G, runs, run, m0, n0)) continue;
+                const int nk = (runs[run].D + kBK - 1) / kBK;
+                // the epilogue has read the previous tile's accumulators
+                if (it > 0 && !mbar_wait(smem_u32(&tempty_bar), (uint32_t)((it - 1) & 1))) {
+                    abort_all(status);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" : : : "memory");
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = (int)(g % Cfg::kStages);
+                    if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((g / Cfg::kStages) & 1))) {
+                        abort_all(status);
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" : : : "memory");
+                    const uint64_t dah = umma_desc_sw128(stage_a_hi(s)), dal = umma_desc_sw128(stage_a_lo(s));
+                    const uint64_t dbh = umma_desc_sw128(stage_b_hi(s)), dbl = umma_desc_sw128(stage_b_lo(s));
+                    // accumulators: [0] corrections, [1 + kb mod kMainAcc] main products
+                    const uint32_t t_corr = tmem, t_main = tmem + (uint32_t)(BN * (1 + kb % kMainAcc));
+                    const bool main_fresh = kb < kMainAcc;
+#pragma unroll
+                    for (int ks = 0; ks < kBK / 16; ++ks) {
+                        // a K step of 16 fp16 = 32 bytes = 2 in the descriptor's address field
+                        const uint64_t o = (uint64_t)(2 * ks);
+                        umma_f16_ss(t_corr, dal + o, dbh + o, Cfg::kIdesc, (kb > 0 || ks > 0) ? 1u : 0u);
+                        umma_f16_ss(t_corr, dah + o, dbl + o, Cfg::kIdesc, 1u);
+                        umma_f16_ss(t_main, dah + o, dbh + o, Cfg::kIdesc, (!main_fresh || ks > 0) ? 1u : 0u);
+                    }
+                    umma_commit(smem_u32(&empty_bar[s]));
+                }
+                if (aborted()) break;
+                umma_commit(smem_u32(&tfull_bar));
+                ++it;
+            }
+            // every MMA issued has completed before the CTA frees TMEM
+            umma_commit(smem_u32(&drain_bar));
+            mbar_wait(smem_u32(&drain_bar), 0u);
+        }
+    } else {
+        // ---- epilogue: warp w takes candidate rows m0 + 32 (w mod 4) + lane
+        // (its TMEM lanes) and the column quarter w / 4 (SW = BN / 4 columns);
+        // the quarters of a row are combined in column order through shared
+        // memory by the warps of quarter 0
+        constexpr int SW = BN / 4;
+        const int quarter = warp & 3, split = warp >> 2;
+        const int rt = 32 * quarter + lane;
+        int it = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+            int run, m0, n0;
+            if (!tile_of(t, G, runs, run, m0, n0)) continue;
+            const BigRun& R = runs[run];
+            const int nk = (R.D + kBK - 1) / kBK;
+            // every epilogue warp takes the same decision (a barrier with an
+            // AND reduction), so none of them is left waiting at the named
+            // barriers below when another gives up
+            const bool ok = !aborted() && mbar_wait(smem_u32(&tfull_bar), (uint32_t)(it & 1));
+            uint32_t all_ok;
+            asm volatile(
+                "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
+                " selp.u32 %0, 1, 0, q;\n}\n"
+                : "=r"(all_ok)
+                : "r"(ok ? 1u : 0u), "r"(32 * kEpiWarps)
+                : "memory");
+            if (!all_ok) {
+                if (threadIdx.x == 0) abort_all(status);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" : : : "memory");
-            const uint64_t dah = umma_desc_sw128(stage_a_hi(s)), dal = umma_desc_sw128(stage_a_lo(s));
-            const uint64_t dbh = umma_desc_sw128(stage_b_hi(s)), dbl = umma_desc_sw128(stage_b_lo(s));
-            // accumulators: [0] corrections, [1 + kb mod kMainAcc] main products
-            const uint32_t t_corr = tmem, t_main = tmem + (uint32_t)(BN * (1 + kb % kMainAcc));
-            const bool main_fresh = kb < kMainAcc;
-#pragma unroll
-            for (int ks = 0; ks < kBK / 16; ++ks) {
-                // a K step of 16 fp16 = 32 bytes = 2 in the descriptor's address field
-                const uint64_t o = (uint64_t)(2 * ks);
-                umma_f16_ss(t_corr, dal + o, dbh + o, Cfg::kIdesc, (kb > 0 || ks > 0) ? 1u : 0u);
-                umma_f16_ss(t_corr, dah + o, dbl + o, Cfg::kIdesc, 1u);
-                umma_f16_ss(t_main, dah + o, dbh + o, Cfg::kIdesc, (!main_fresh || ks > 0) ? 1u : 0u);
-            }
-            umma_commit(smem_u32(&empty_bar[s]));
-        }
-        umma_commit(smem_u32(&done_bar));
-    }
-    __syncwarp();
-    // epilogue: warp w takes candidate rows m0 + 32 (w mod 4) + lane (its TMEM
-    // lanes) and the column quarter w / 4 (SW = BN / 4 columns); the four
-    // quarters of a row are then combined in column order through shared memory
-    constexpr int SW = BN / 4;
-    const int quarter = warp & 3, split = warp >> 2;
-    const bool ok = mbar_wait(smem_u32(&done_bar), 0u) && atomicAdd(&s_err, 0) == 0;
-    asm volatile("tcgen05.fence::after_thread_sync;" : : : "memory");
-    const int rt = 32 * quarter + lane, row = m0 + rt;
-    const int c0 = n0 + SW * split;
-    const EpiForm E{R.D, R.form, R.s1, R.s2};
-    float s1 = 0.f, s2 = E.form == kGriewank ? 1.f : 0.f, prev = 0.f;
-    bool have_prev = false;
-    float zfirst = 0.f;
-    const float zsc = R.zsc;
-    const bool all_ok = __syncthreads_and(ok) != 0;
-    if (all_ok) {
-        const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(SW * split);
-        const int used = nk < kMainAcc ? nk : kMainAcc;
-        uint32_t r0[SW], r1[SW];
-        float z[SW];
-        tmem_ld_nowait(ta, r0);                              // corrections
-        tmem_ld_nowait(ta + (uint32_t)BN, r1);               // main accumulator 0
-        tmem_wait(r0, r1);
-#pragma unroll
-        for (int i = 0; i < SW; ++i) z[i] = __uint_as_float(r0[i]) + __uint_as_float(r1[i]);
-        if (used > 1) {
-            tmem_ld_nowait(ta + (uint32_t)(2 * BN), r0);
-            if (used > 2) tmem_ld_nowait(ta + (uint32_t)(3 * BN), r1);
+            const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(SW * split);
+            const int used = nk < kMainAcc ? nk : kMainAcc;
+            // corrections + main accumulators in the order 0, 1, 2 (one
+            // buffer in flight at a time keeps the registers within budget)
+            uint32_t r0[SW], r1[SW];
+            float z[SW];
+            tmem_ld_nowait(ta, r0);
+            tmem_ld_nowait(ta + (uint32_t)BN, r1);
             tmem_wait(r0, r1);
 #pragma unroll
-            for (int i = 0; i < SW; ++i) z[i] += __uint_as_float(r0[i]) + (used > 2 ? __uint_as_float(r1[i]) : 0.f);
-        }
+            for (int i = 0; i < SW; ++i) z[i] = __uint_as_float(r0[i]) + __uint_as_float(r1[i]);
+            for (int a = 1; a < used; ++a) {
+                tmem_ld_nowait(ta + (uint32_t)((a + 1) * BN), r1);
+                tmem_wait(r1);
 #pragma unroll
-        for (int i = 0; i < SW; ++i) z[i] *= zsc;
-        zfirst = z[0];
-        if (c0 < E.D) epi_terms<SW>(z, c0, E, ew_s, n0, s1, s2, prev, have_prev);
-        s_quart[split][rt] = make_float2(s1, s2);
-        s_edge[split][rt] = make_float2(zfirst, prev);
-    } else if (threadIdx.x == 0) {
-        set_status(R.status, 4 /* APO_ERR_TIMEOUT */);
-    }
-    __syncthreads();
-    if (all_ok && split == 0 && row < R.ps) {
-        // quarters in column order; the Rosenbrock pair (n, n + 1) across a
-        // quarter boundary is added here
-        float a = s_quart[0][rt].x, b = s_quart[0][rt].y;
-        float zl = s_edge[0][rt].y;
-        for (int c = 1; c < 4 && n0 + SW * c < E.D; ++c) {
-            const float2 q = s_quart[c][rt];
-            const float2 ed = s_edge[c][rt];
-            if (E.form == kGriewank) {
-                a += q.x;
-                b *= q.y;
-            } else {
-                a += q.x;
-                b += q.y;
+                for (int i = 0; i < SW; ++i) z[i] += __uint_as_float(r1[i]);
             }
-            const int n = n0 + SW * c - 1;
-            if (E.form != kHGBat && E.form != kGriewank && n >= E.s1 && n + 1 < E.s2) {
-                const float u = ed.x - zl * zl;
-                const float v = zl - 1.f;
-                a += 100.f * u * u + v * v;
+            // the accumulators are free for the next tile's MMAs
+            asm volatile("tcgen05.fence::before_thread_sync;" : : : "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" : : "r"(smem_u32(&tempty_bar)) : "memory");
+            ++it;
+
+            const int row = m0 + rt;
+            const int c0 = n0 + SW * split;
+            const EpiForm E{R.D, R.form, R.s1, R.s2};
+            const float zsc = R.zsc;
+            float s1 = 0.f, s2 = E.form == kGriewank ? 1.f : 0.f, prev = 0.f;
+            bool have_prev = false;
+#pragma unroll
+            for (int i = 0; i < SW; ++i) z[i] *= zsc;
+            const float zfirst = z[0];
+            if (c0 < E.D) epi_terms<SW>(z, c0, E, R.ew, s1, s2, prev, have_prev);
+            s_quart[split][rt] = make_float2(s1, s2);
+            s_edge[split][rt] = make_float2(zfirst, prev);
+            asm volatile("bar.sync 1, %0;" : : "r"(32 * kEpiWarps) : "memory");
+            if (split == 0 && row < R.ps) {
+                // quarters in column order; the Rosenbrock pair (n, n + 1)
+                // across a quarter boundary is added here
+                float a = s_quart[0][rt].x, b = s_quart[0][rt].y;
+                float zl = s_edge[0][rt].y;
+                for (int c = 1; c < 4 && n0 + SW * c < E.D; ++c) {
+                    const float2 q = s_quart[c][rt];
+                    const float2 ed = s_edge[c][rt];
+                    a += q.x;
+                    if (E.form == kGriewank) b *= q.y;
+                    else b += q.y;
+                    const int n = n0 + SW * c - 1;
+                    if (E.form != kHGBat && E.form != kGriewank && n >= E.s1 && n + 1 < E.s2) {
+                        const float u = ed.x - zl * zl;
+                        const float v = zl - 1.f;
+                        a += 100.f * u * u + v * v;
+                    }
+                    zl = ed.y;
+                }
+                const size_t o = (size_t)row * R.ntiles + n0 / BN;
+                R.part[o] = make_float2(a, b);
+                R.zedge[o] = make_float2(s_edge[0][rt].x, zl);   // z at n0 and at the tile's last column
             }
-            zl = ed.y;
+            asm volatile("bar.sync 1, %0;" : : "r"(32 * kEpiWarps) : "memory");
         }
-        const size_t o = (size_t)row * R.ntiles + blockIdx.x;
-        R.part[o] = make_float2(a, b);
-        R.zedge[o] = make_float2(s_edge[0][rt].x, zl);   // z at n0 and at the tile's last column
     }
     asm volatile("tcgen05.fence::before_thread_sync;" : : : "memory");
     __syncthreads();
-    // on an error, the loads already issued must land before the CTA leaves
-    if (!ok && warp == 0 && lane == 0) {
-        for (int kb = max(0, issued - Cfg::kStages); kb < issued; ++kb)
-            mbar_wait(smem_u32(&full_bar[kb % Cfg::kStages]), (uint32_t)((kb / Cfg::kStages) & 1));
+    // on an abort, the loads already issued must land before the CTA leaves
+    if (aborted() && warp == kEpiWarps && lane == 0) {
+        for (long long g = issued > Cfg::kStages ? issued - Cfg::kStages : 0; g < issued; ++g)
+            mbar_wait(smem_u32(&full_bar[g % Cfg::kStages]), (uint32_t)((g / Cfg::kStages) & 1));
     }
-    if (warp == 2)
+    __syncthreads();
+    if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" : : "r"(tmem), "r"(Cfg::kCols)
                      : "memory");
 }
@@ -757,8 +824,13 @@ cudaError_t launch_gemm(const BigRun* d_runs, const BigMaps& maps, int n_runs, i
     const int smem = kGemmSmem + 1024;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(max_ntiles, (max_ps + kBM - 1) / kBM, n_runs);
-    fn<<<grid, kGemmThreads, smem, st>>>(d_runs, maps);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const TileGrid G{(max_ps + kBM - 1) / kBM, max_ntiles, BN};
+    const int n_tiles = G.max_mt * G.max_nt * n_runs;
+    // persistent: one CTA per SM (fewer when there are fewer tiles)
+    fn<<<std::min(n_tiles, sms), kGemmThreads, smem, st>>>(d_runs, maps, G, n_tiles);
     return cudaGetLastError();
 }
 

@@ -142,6 +142,14 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&a)[N], uint32_t (&b)[N])
     for (int i = 0; i < N; ++i) asm volatile("" : "+r"(a[i]), "+r"(b[i]));
 }
 
+template <int N>
+__device__ __forceinline__ void tmem_wait(uint32_t (&a)[N])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : : : "memory");
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm volatile("" : "+r"(a[i]));
+}
+
 // 32 consecutive accumulator columns of the calling thread's TMEM lane
 // (warp w reads lanes 32 (w mod 4) .. + 31).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
