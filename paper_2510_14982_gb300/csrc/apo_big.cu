@@ -432,7 +432,7 @@ __device__ __forceinline__ void epi_terms(const float (&z)[W], int n, const EpiF
                 s1 += 100.f * a * a + b * b;
             }
         } else {
-            s1 += v * v - 10.f * cospif(2.f * v) + 10.f;
+            s1 += v * v - 10.f * cos2pi(v) + 10.f;
         }
         prev = v;
         have_prev = true;

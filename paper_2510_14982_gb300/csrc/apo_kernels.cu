@@ -224,10 +224,11 @@ __device__ __forceinline__ void run_one(const ApoRun& R, int local, unsigned cha
         const bool curve_w = local == 0 && tid == 0 && R.curve != nullptr;
         const FitT curve_v = curve_w ? ldst(Fs[cur] + perm[0], res) : (FitT)0;
 
+        const IterScal is = iter_scal(R, t);
         for (int c0 = r0; c0 < r1; c0 += CH) {
             const int rows = min(CH, r1 - c0);
             for (int row = warp; row < rows; row += nw)
-                gen_step_row<FitT, QPL>(R, S, Xs[cur], nullptr, Fs[cur], perm, res, true, t, c0 + row,
+                gen_step_row<FitT, QPL>(R, S, Xs[cur], nullptr, Fs[cur], perm, res, true, t, is, c0 + row,
                                         dr_state(R, t, c0 + row), row);
             __syncthreads();
             eval_chunk<FitT>(R, S, rows);
@@ -388,12 +389,36 @@ __device__ __forceinline__ void copy_cg(T* dst, const T* __restrict__ src, int n
     }
 }
 
-// Inclusive prefix sums of a[0, n) in place, by all threads of the CTA; each
-// warp scans a contiguous range, offset by the totals of the warps before it
-// (wsum: one int per warp).
+// Inclusive prefix sums of a[0, n) in place, called by all threads of the
+// CTA.  Up to 32 x 16 elements are scanned by warp 0 alone: each lane sums a
+// contiguous run of at most 16, one shuffle scan over the 32 run totals gives
+// each run its offset, and a single CTA barrier publishes the result.
+// Longer arrays: each warp scans a contiguous range, offset by the totals of
+// the warps before it (wsum: one int per warp).
 __device__ __forceinline__ void block_scan_inclusive(int* a, int n, int* wsum)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (n <= 32 * 16) {
+        if (warp == 0) {
+            const int per = (n + 31) >> 5;
+            const int b = min(n, lane * per), e = min(n, b + per);
+            int tot = 0;
+            for (int i = b; i < e; ++i) tot += a[i];
+            int incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            int run = incl - tot;
+            for (int i = b; i < e; ++i) {
+                run += a[i];
+                a[i] = run;
+            }
+        }
+        __syncthreads();
+        return;
+    }
     const int per = (n + nw - 1) / nw;
     const int b = min(n, warp * per), e = min(n, b + per);
     int carry = 0;
@@ -491,21 +516,19 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
 
     // Greedy writes of the chunk at c0 (rows rows, fitness and rows in Xc):
     // the kept fitness of each row to Fd, and the accepted rows to their
-    // slots' other buffers, one 16-byte group per thread.
+    // slots' other buffers, a row per warp in 16-byte groups.
     auto write_chunk = [&](int c0, int rows, FitT* Fd) {
         for (int row = tid; row < rows; row += NT) {
             const FitT fo = S.rowF[CH + row], fn = S.rowF[row];
             Fd[perm[pos_of(c0 + row)] & kSlotMask] = fn < fo ? fn : fo;
         }
         const int g4 = Dp >> 2;
-        for (int i = tid; i < rows * g4; i += NT) {
-            const int row = i / g4, v = i - row * g4;
-            if (S.rowF[row] < S.rowF[CH + row]) {
-                const uint32_t e = perm[pos_of(c0 + row)];
-                const float4* src = reinterpret_cast<const float4*>(S.Xc + (size_t)row * Dp);
-                float4* dst = reinterpret_cast<float4*>(Xs[(e >> 31) ^ 1u] + (size_t)(e & kSlotMask) * Dp);
-                dst[v] = src[v];
-            }
+        for (int row = warp; row < rows; row += nw) {
+            if (!(S.rowF[row] < S.rowF[CH + row])) continue;
+            const uint32_t e = perm[pos_of(c0 + row)];
+            const float4* src = reinterpret_cast<const float4*>(S.Xc + (size_t)row * Dp);
+            float4* dst = reinterpret_cast<float4*>(Xs[(e >> 31) ^ 1u] + (size_t)(e & kSlotMask) * Dp);
+            for (int v = lane; v < g4; v += 32) dst[v] = src[v];
         }
     };
     int held_c0 = 0, held_rows = 0;   // greedy writes held for barrier A
@@ -625,10 +648,11 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
         }
 
         // the own positions: generate, evaluate, replace
+        const IterScal is = iter_scal(R, t);
         for (int c0 = 0; c0 < nown; c0 += CH) {
             const int rows = min(CH, nown - c0);
             for (int row = warp; row < rows; row += nw)
-                gen_step_row<FitT, QPL>(R, S, Xs[0], Xs[1], Fs[cur], perm, false, false, t, pos_of(c0 + row),
+                gen_step_row<FitT, QPL>(R, S, Xs[0], Xs[1], Fs[cur], perm, false, false, t, is, pos_of(c0 + row),
                                         drs[c0 + row], row);
             __syncthreads();
             if (!evaluate(rows)) return;

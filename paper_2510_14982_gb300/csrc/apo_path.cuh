@@ -279,7 +279,7 @@ __device__ __forceinline__ float seg_value(const float* z, int zs, const DevComp
                 s += 100.f * a * a + b * b;
             }
         } else {
-            s += v * v - 10.f * cospif(2.f * v) + 10.f;
+            s += v * v - 10.f * cos2pi(v) + 10.f;
         }
     }
     return warp_sum(s);
@@ -323,7 +323,7 @@ __device__ __forceinline__ void seg_values(const float* const (&z)[NR], const De
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
                 const float v = z[i][d];
-                s[i] += v * v - 10.f * cospif(2.f * v) + 10.f;
+                s[i] += v * v - 10.f * cos2pi(v) + 10.f;
             }
         }
     }
@@ -527,6 +527,18 @@ __device__ __forceinline__ void gen_init_row(const ApoRun& R, const Smem<FitT>& 
     }
 }
 
+// The iteration's scalars of Eq. 7, Eq. 9 and Eq. 11-13 (p_ah threshold, the
+// foraging factor's scale and the neighbourhood scale), loaded once per
+// iteration by the caller rather than once per candidate row.
+struct IterScal {
+    uint32_t thr_ah;
+    float fsc, nsc;
+};
+__device__ __forceinline__ IterScal iter_scal(const ApoRun& R, int t)
+{
+    return IterScal{R.thr_ah[t], R.fsc[t], R.nsc[t]};
+}
+
 // One candidate (rank r, 0-based) by one warp: mode selection (Eq. 12-13,
 // Algorithm 1), masks (Eq. 3, Eq. 5), dormancy (Eq. 1), reproduction
 // (Eq. 2), autotrophic (Eq. 6-7) or heterotrophic (Eq. 8-10) foraging, then
@@ -541,7 +553,8 @@ __device__ __forceinline__ void gen_init_row(const ApoRun& R, const Smem<FitT>& 
 template <typename FitT, int QPL>
 __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* __restrict__ X,
                              const float* __restrict__ X1, const FitT* __restrict__ F, const uint32_t* perm,
-                             bool res, bool keep_old, int t, int r, uint32_t drs, int row, int cand = 0)
+                             bool res, bool keep_old, int t, const IterScal& is, int r, uint32_t drs, int row,
+                             int cand = 0)
 {
     // candidate c of the surrogate-assisted form draws from slots | (c << 8);
     // c = 0 is the plain candidate
@@ -549,10 +562,8 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     const int lane = threadIdx.x & 31;
     const int D = R.prob.D, Dp = R.prob.Dp, ps = R.ps, np = R.np;
     const uint32_t seed = R.seed, run = R.run;
-    // the iteration's scalars (Eq. 7, Eq. 9, Eq. 11) are requested first, so
-    // that their latency overlaps the draws
-    const uint32_t thr_ah = R.thr_ah[t];
-    const float fsc = R.fsc[t], nsc = R.nsc[t];
+    const uint32_t thr_ah = is.thr_ah;
+    const float fsc = is.fsc, nsc = is.nsc;
     const float inv_np = 1.f / (float)np;
     // Per-protozoon draws, from lanes jb + u: u = 0 SCAL, u = 1 SCAL2,
     // u = 2 + k PAIR k.  The last per-dimension call of a lane covers pairs

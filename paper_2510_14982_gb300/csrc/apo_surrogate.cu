@@ -453,11 +453,12 @@ __global__ void __launch_bounds__(kSurThreads) surr_gen_kernel(const ApoRun* __r
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int D = R.prob.D, Dp = R.prob.Dp, CH = R.plan.chunk;
     const int nrow = R.ps * k;
+    const IterScal is = iter_scal(R, t);
     for (int c0 = blockIdx.x * CH; c0 < nrow; c0 += gridDim.x * CH) {
         const int rows = min(CH, nrow - c0);
         for (int row = warp; row < rows; row += nw) {
             const int q = c0 + row, r = q / k, c = q - r * k;
-            gen_step_row<float, QPL>(R, S, X, nullptr, F, S.perm[0], false, false, t, r, dr_state(R, t, r), row, c);
+            gen_step_row<float, QPL>(R, S, X, nullptr, F, S.perm[0], false, false, t, is, r, dr_state(R, t, r), row, c);
             __syncwarp();
             for (int d = lane; d < Dp; d += 32) Xcand[(size_t)q * Dp + d] = S.Xc[(size_t)row * Dp + d];
             if (Xin)
