@@ -230,6 +230,21 @@ __device__ __forceinline__ float cos2pi(float v)
     return flip ? -p : p;
 }
 
+// The per-coordinate terms of the chained Rosenbrock form (the pair (z_d,
+// z_{d+1})) and of the Rastrigin form, with every multiply-add written out,
+// so that each kernel that evaluates them (whatever the compiler would fuse
+// in its context) rounds them the same way.
+__device__ __forceinline__ float rosen_term(float v, float vn)
+{
+    const float a = fmaf(-v, v, vn);
+    const float b = v - 1.f;
+    return fmaf(100.f * a, a, b * b);
+}
+__device__ __forceinline__ float rast_term(float v)
+{
+    return fmaf(v, v, fmaf(-10.f, cos2pi(v), 10.f));
+}
+
 // ------------------------------------------------------- fitness ordering
 __device__ __forceinline__ uint32_t ord_key(float f)
 {

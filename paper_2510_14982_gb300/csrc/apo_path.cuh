@@ -274,12 +274,10 @@ __device__ __forceinline__ float seg_value(const float* z, int zs, const DevComp
             s = fmaf(ew[d] * v, v, s);
         } else if (d < C.s2) {
             if (d + 1 < C.s2) {
-                const float a = z[(size_t)(d + 1) * zs] - v * v;
-                const float b = v - 1.f;
-                s += 100.f * a * a + b * b;
+                s += rosen_term(v, z[(size_t)(d + 1) * zs]);
             }
         } else {
-            s += v * v - 10.f * cos2pi(v) + 10.f;
+            s += rast_term(v);
         }
     }
     return warp_sum(s);
@@ -313,17 +311,13 @@ __device__ __forceinline__ void seg_values(const float* const (&z)[NR], const De
             if (d + 1 < C.s2) {
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
-                    const float v = z[i][d];
-                    const float a = z[i][d + 1] - v * v;
-                    const float b = v - 1.f;
-                    s[i] += 100.f * a * a + b * b;
+                    s[i] += rosen_term(z[i][d], z[i][d + 1]);
                 }
             }
         } else {
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
-                const float v = z[i][d];
-                s[i] += v * v - 10.f * cos2pi(v) + 10.f;
+                s[i] += rast_term(z[i][d]);
             }
         }
     }
@@ -333,6 +327,48 @@ __device__ __forceinline__ void seg_values(const float* const (&z)[NR], const De
         for (int i = 0; i < NR; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], off);
 #pragma unroll
     for (int i = 0; i < NR; ++i) out[i] = s[i];
+}
+
+// Objective terms of one row's z values z[0..W-1] at output dimensions n ..
+// n + W - 1 (those below E.D), accumulated into (s1, s2) by the
+// large-dimension GEMM's epilogue, which reads a row's z from the
+// accumulator column by column.
+// Segment forms: [0, s1) ew z^2, [s1, s2) the Rosenbrock chain (the pair
+// (n - 1, n) is added at n, with prev = z_{n-1}), [s2, D) Rastrigin.  HGBat:
+// (sum u (u - 1), sum u^2), u = z / 20.  Griewank: (sum y^2, prod cos(y ew)),
+// y = 6 z.  ew is read through the read-only cache.
+struct EpiForm {
+    int D, form, s1, s2;
+};
+
+template <int W>
+__device__ __forceinline__ void epi_terms(const float (&z)[W], int n, const EpiForm& E, const float* __restrict__ ew,
+                                          float& s1, float& s2, float& prev, bool& have_prev)
+{
+    auto ld_ew = [&](int c) { return __ldg(ew + c); };
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const int c = n + i;
+        if (c >= E.D) break;
+        const float v = z[i];
+        if (E.form == kHGBat) {
+            const float u = v * 0.05f;
+            s1 = fmaf(u, u, s1 - u);
+            s2 = fmaf(u, u, s2);
+        } else if (E.form == kGriewank) {
+            const float y = 6.f * v;
+            s1 = fmaf(y, y, s1);
+            s2 *= cospif(y * ld_ew(c));   // ew = 1 / (pi sqrt(c + 1))
+        } else if (c < E.s1) {
+            s1 = fmaf(ld_ew(c) * v, v, s1);
+        } else if (c < E.s2) {
+            if (have_prev && c - 1 >= E.s1) s1 += rosen_term(prev, v);
+        } else {
+            s1 += rast_term(v);
+        }
+        prev = v;
+        have_prev = true;
+    }
 }
 
 // Objective of the rows [0, rows) of the Z tile (rows Np apart) into rowF:
