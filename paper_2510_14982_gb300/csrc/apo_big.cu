@@ -397,6 +397,44 @@ struct GemmCfg {
     static_assert((kCols & (kCols - 1)) == 0 && kCols <= 512, "TMEM allocation");
 };
 
+// Objective terms of one row's z values z[0..31] at columns n .. n + 31.
+// Segment forms: [0, s1) ew z^2, [s1, s2) the Rosenbrock chain (the pair
+// (n - 1, n) is added at n, with prev = z_{n-1}), [s2, D) Rastrigin.  HGBat:
+// (sum u (u - 1), sum u^2), u = z / 20.  Griewank: (sum y^2, prod cos(y ew)),
+// y = 6 z.
+struct EpiForm {
+    int D, form, s1, s2;
+};
+
+template <int W>
+__device__ __forceinline__ void epi_terms(const float (&z)[W], int n, const EpiForm& E, const float* __restrict__ ew,
+                                          float& s1, float& s2, float& prev, bool& have_prev)
+{
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const int c = n + i;
+        if (c >= E.D) break;
+        const float v = z[i];
+        if (E.form == kHGBat) {
+            const float u = v * 0.05f;
+            s1 = fmaf(u, u, s1 - u);
+            s2 = fmaf(u, u, s2);
+        } else if (E.form == kGriewank) {
+            const float y = 6.f * v;
+            s1 = fmaf(y, y, s1);
+            s2 *= cospif(y * __ldg(ew + c));   // ew = 1 / (pi sqrt(c + 1))
+        } else if (c < E.s1) {
+            s1 = fmaf(__ldg(ew + c) * v, v, s1);
+        } else if (c < E.s2) {
+            if (have_prev && c - 1 >= E.s1) s1 += rosen_term(prev, v);
+        } else {
+            s1 += rast_term(v);
+        }
+        prev = v;
+        have_prev = true;
+    }
+}
+
 // Tile t of a launch (N tiles fastest, then M tiles, then runs): run, m0, n0;
 // false for tiles outside the run's population or dimension.
 struct TileGrid {

@@ -329,48 +329,6 @@ __device__ __forceinline__ void seg_values(const float* const (&z)[NR], const De
     for (int i = 0; i < NR; ++i) out[i] = s[i];
 }
 
-// Objective terms of one row's z values z[0..W-1] at output dimensions n ..
-// n + W - 1 (those below E.D), accumulated into (s1, s2) by the
-// large-dimension GEMM's epilogue, which reads a row's z from the
-// accumulator column by column.
-// Segment forms: [0, s1) ew z^2, [s1, s2) the Rosenbrock chain (the pair
-// (n - 1, n) is added at n, with prev = z_{n-1}), [s2, D) Rastrigin.  HGBat:
-// (sum u (u - 1), sum u^2), u = z / 20.  Griewank: (sum y^2, prod cos(y ew)),
-// y = 6 z.  ew is read through the read-only cache.
-struct EpiForm {
-    int D, form, s1, s2;
-};
-
-template <int W>
-__device__ __forceinline__ void epi_terms(const float (&z)[W], int n, const EpiForm& E, const float* __restrict__ ew,
-                                          float& s1, float& s2, float& prev, bool& have_prev)
-{
-    auto ld_ew = [&](int c) { return __ldg(ew + c); };
-#pragma unroll
-    for (int i = 0; i < W; ++i) {
-        const int c = n + i;
-        if (c >= E.D) break;
-        const float v = z[i];
-        if (E.form == kHGBat) {
-            const float u = v * 0.05f;
-            s1 = fmaf(u, u, s1 - u);
-            s2 = fmaf(u, u, s2);
-        } else if (E.form == kGriewank) {
-            const float y = 6.f * v;
-            s1 = fmaf(y, y, s1);
-            s2 *= cospif(y * ld_ew(c));   // ew = 1 / (pi sqrt(c + 1))
-        } else if (c < E.s1) {
-            s1 = fmaf(ld_ew(c) * v, v, s1);
-        } else if (c < E.s2) {
-            if (have_prev && c - 1 >= E.s1) s1 += rosen_term(prev, v);
-        } else {
-            s1 += rast_term(v);
-        }
-        prev = v;
-        have_prev = true;
-    }
-}
-
 // Objective of the rows [0, rows) of the Z tile (rows Np apart) into rowF:
 // warp w takes rows w, w + nw, ..., w + 7 nw together (one pass for up to
 // 8 nw rows).

@@ -1,22 +1,20 @@
 // apo_umma.cuh -- the rotation z = M (x - o) of the cooperative grid kernel
 // on the fifth-generation tensor cores (tcgen05, accumulator in tensor
-// memory), for a single rotated component with D <= kTcM, and the objective
-// read straight from the accumulator.
+// memory), for a single rotated component with D <= kTcM.
 //
-// A chunk of kTcN candidate rows is one MMA tile with the candidates as the
-// M side (kTcM rows read, the rows past kTcN unused) and the output
-// dimensions as the N side (Np):
-//   acc[row][n] = sum_k y[row][k] B[n][k],   y = ysc (x - o),  B = msc M,
-// so TMEM lane row, column n holds z[row][n] / zsc.  Both operands are fp16
+// A chunk of kTcN candidate rows is one MMA tile with the rotation as the M
+// side (kTcM rows n) and the candidates as the N side:
+//   acc[n][row] = sum_k B[n][k] y[row][k],   y = ysc (x - o),  B = msc M,
+// so TMEM lane n, column row holds z[row][n] / zsc.  Both operands are fp16
 // hi + lo parts in shared memory in the canonical K-major layout (umma_off):
 // the rotation's (TA) loaded once per launch, the candidates' (TY) split from
 // the chunk per chunk.  One thread issues three MMAs per K = 16 step,
 // y_lo B_hi, y_hi B_lo, y_hi B_hi, in that order, accumulating in fp32 (the
 // dropped y_lo B_lo is below 2^-22 of a product), and commits them to an
-// mbarrier that every thread waits on with a time limit.  Each thread then
-// reads one candidate's z over a quarter of the output dimensions with
-// tcgen05.ld, scaled by zsc, and sums its objective terms; the quarters are
-// combined in column order through shared memory.
+// mbarrier that every thread waits on with a time limit.  The accumulator is
+// then read with tcgen05.ld into the row-major Z tile, scaled by zsc, for
+// the objective epilogue.  The operand values and the MMA sequence are those
+// of the mma.sync rotation (tile_gemm_f16x3).
 #pragma once
 
 #include "apo_path.cuh"
@@ -24,15 +22,12 @@
 namespace apo {
 
 // instruction descriptor: fp32 accumulator, f16 A and B, both K-major,
-// M = kTcM candidate rows, N = Np output dimensions (a multiple of 16)
-__device__ __forceinline__ uint32_t rot_idesc(int Np)
-{
-    return (1u << 4) | ((uint32_t)(Np >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
-}
+// N = kTcN, M = kTcM
+constexpr uint32_t kRotIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
 constexpr unsigned long long kMmaTimeoutNs = 1000000000ull;   // 1 s per wait
 
 struct TcState {
-    uint32_t tmem;    // accumulator: Np of kTcCols columns x kTcM lanes
+    uint32_t tmem;    // accumulator: kTcN of kTcCols columns x kTcM lanes
     uint32_t mbar;    // shared address of the completion mbarrier
     uint32_t phase;   // commits waited for so far
 };
@@ -96,21 +91,14 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
     }
 }
 
-__device__ __forceinline__ void umma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate)
+__device__ __forceinline__ void umma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t accumulate)
 {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
         :
-        : "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+        : "r"(tmem), "l"(ad), "l"(bd), "r"(kRotIdesc), "r"(accumulate)
         : "memory");
-}
-
-// One accumulator column of the calling thread's TMEM lane (warp w reads
-// lanes 32 (w mod 4) .. + 31), without waiting.
-__device__ __forceinline__ void tmem_ld1(uint32_t taddr, uint32_t& a)
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(a) : "r"(taddr));
 }
 
 // Evaluates the candidate rows Xc[0, rows) (rows <= kTcN) of the single
@@ -163,23 +151,19 @@ __device__ bool eval_chunk_tc(const ApoRun& R, const Smem<FitT>& S, int rows, Tc
     __syncthreads();
     if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" : : : "memory");
-        const uint32_t bh = (uint32_t)__cvta_generic_to_shared(S.TA);
-        const uint32_t bl = bh + (uint32_t)(Np * Np * 2);
-        // A K step advances every operand by two core matrices (256 bytes),
+        const uint32_t ah = (uint32_t)__cvta_generic_to_shared(S.TA);
+        const uint32_t al = ah + (uint32_t)(Np * Np * 2);
+        // a K step advances every operand by two core matrices (256 bytes),
         // i.e. 16 in the descriptor's address field (which cannot carry:
-        // shared addresses stay below 2^18).  The A side reads kTcM candidate
-        // rows: rows past kTcN of the hi part fall into the lo part, those of
-        // the lo part into the tables after TY; their accumulator rows are
-        // never read.
-        uint64_t dyh = umma_kdesc((uint32_t)__cvta_generic_to_shared(yh), Np);
-        uint64_t dyl = umma_kdesc((uint32_t)__cvta_generic_to_shared(yl), Np);
-        uint64_t dbh = umma_kdesc(bh, Np), dbl = umma_kdesc(bl, Np);
-        const uint32_t idesc = rot_idesc(Np);
+        // shared addresses stay below 2^18)
+        uint64_t dah = umma_kdesc(ah, Np), dal = umma_kdesc(al, Np);
+        uint64_t dbh = umma_kdesc((uint32_t)__cvta_generic_to_shared(yh), Np);
+        uint64_t dbl = umma_kdesc((uint32_t)__cvta_generic_to_shared(yl), Np);
         for (int s = 0; s < (Np >> 4); ++s) {
-            umma_f16(st.tmem, dyl, dbh, idesc, s > 0 ? 1u : 0u);
-            umma_f16(st.tmem, dyh, dbl, idesc, 1u);
-            umma_f16(st.tmem, dyh, dbh, idesc, 1u);
-            dyh += 16u; dyl += 16u; dbh += 16u; dbl += 16u;
+            umma_f16(st.tmem, dah, dbl, s > 0 ? 1u : 0u);
+            umma_f16(st.tmem, dal, dbh, 1u);
+            umma_f16(st.tmem, dah, dbh, 1u);
+            dah += 16u; dal += 16u; dbh += 16u; dbl += 16u;
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :
@@ -191,100 +175,29 @@ __device__ bool eval_chunk_tc(const ApoRun& R, const Smem<FitT>& S, int rows, Tc
     if (!__syncthreads_and(done)) return false;
     asm volatile("tcgen05.fence::after_thread_sync;" : : : "memory");
 
-    // Objective from the accumulator, in exactly the arithmetic of seg_value
-    // (the evaluation of the other kernels), so that every kernel gives the
-    // same fitness bit for bit: there lane l of a warp accumulates the output
-    // dimensions d = l, l + 32, ... in order, and the 32 lane sums are added
-    // by the xor butterfly (16, 8, 4, 2, 1).  Here warp w takes the candidate
-    // rows 32 (w mod 4) + lane (its TMEM lanes) and plays the lanes
-    // l = l0 + 8 m (m = 0..3) for l0 = 2 q, 2 q + 1 (q = w / 4), reading one
-    // accumulator column per load; the butterfly's first two levels (xor 16,
-    // xor 8) stay within the thread, and its last three combine the eight
-    // level-2 values of a row through shared memory (the TY region, free once
-    // the MMAs have completed).
+    // accumulator -> Z tile: warp w reads TMEM lanes 32 (w & 3) .. + 31
+    // (n = lane) and 16 columns (candidate rows) per load
     const float zsc = C.zsc;
-    const int form = C.form;
-    const bool f2 = form == kHGBat || form == kGriewank;
-    float* w1 = reinterpret_cast<float*>(S.TY);   // [8][kTcN] level-2 values of the (first) sum
-    float* w2 = w1 + 8 * kTcN;                    // [8][kTcN] of the second sum (HGBat, Griewank)
-    const int row = 32 * (warp & 3) + lane;
-    const uint32_t tl = st.tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-    for (int q = warp >> 2; q < 4; q += nw >> 2) {
-        float a[8], c[8];   // lane l = 2 q + (i & 1) + 8 (i >> 1)
+    const int n = 32 * (warp & 3) + lane;
+    for (int cg = warp >> 2; cg < kTcN / 16; cg += nw >> 2) {
+        uint32_t v[16];
+        const uint32_t taddr = st.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * cg);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" : : : "memory");
+        if (n < Np) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            a[i] = 0.f;
-            c[i] = form == kGriewank ? 1.f : 0.f;
-        }
-        for (int j = 0; 32 * j < D; ++j) {
-            // columns d0 = 32 j + 8 m + 2 q, d0 + 1, and d0 + 2 (z[d + 1] of
-            // the Rosenbrock chain at d = d0 + 1); the column conditions are
-            // uniform over the warp, and every column read lies below Np
-            uint32_t v[12];
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const int d0 = 32 * j + 8 * m + 2 * q;
-                v[3 * m] = v[3 * m + 1] = v[3 * m + 2] = 0u;
-                if (d0 < Np) {
-                    tmem_ld1(tl + (uint32_t)d0, v[3 * m]);
-                    tmem_ld1(tl + (uint32_t)(d0 + 1), v[3 * m + 1]);
-                }
-                if (d0 + 2 < Np) tmem_ld1(tl + (uint32_t)(d0 + 2), v[3 * m + 2]);
-            }
-            asm volatile("tcgen05.wait::ld.sync.aligned;" : : : "memory");
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int i = 2 * m + e, d = 32 * j + 8 * m + 2 * q + e;
-                    if (d >= D) continue;
-                    const float z = __uint_as_float(v[3 * m + e]) * zsc;
-                    if (form == kHGBat) {
-                        const float u = z * 0.05f;
-                        a[i] = fmaf(u, u, a[i] - u);
-                        c[i] = fmaf(u, u, c[i]);
-                    } else if (form == kGriewank) {
-                        const float y = 6.f * z;
-                        a[i] = fmaf(y, y, a[i]);
-                        c[i] *= cospif(y * S.ew[d]);
-                    } else if (d < C.s1) {
-                        a[i] = fmaf(S.ew[d] * z, z, a[i]);
-                    } else if (d < C.s2) {
-                        if (d + 1 < C.s2) a[i] += rosen_term(z, __uint_as_float(v[3 * m + e + 1]) * zsc);
-                    } else {
-                        a[i] += rast_term(z);
-                    }
-                }
-        }
-        if (row < kTcN) {
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                // levels xor 16 and xor 8: (s_l0 + s_l0+16) + (s_l0+8 + s_l0+24)
-                w1[(2 * q + e) * kTcN + row] = (a[e] + a[4 + e]) + (a[2 + e] + a[6 + e]);
-                if (f2)
-                    w2[(2 * q + e) * kTcN + row] = form == kGriewank ? (c[e] * c[4 + e]) * (c[2 + e] * c[6 + e])
-                                                                      : (c[e] + c[4 + e]) + (c[2 + e] + c[6 + e]);
-            }
+            for (int j = 0; j < 16; ++j) S.Zc[(size_t)(16 * cg + j) * Np + n] = __uint_as_float(v[j]) * zsc;
         }
     }
     // the next chunk's MMAs overwrite the accumulator only after every read
     asm volatile("tcgen05.fence::before_thread_sync;" : : : "memory");
     __syncthreads();
-    // levels xor 4, xor 2, xor 1 as lane 0 adds them
-    auto tree = [&](const float* w, int r, bool prod) {
-        float x[8];
-#pragma unroll
-        for (int l0 = 0; l0 < 8; ++l0) x[l0] = w[l0 * kTcN + r];
-        if (prod) return ((x[0] * x[4]) * (x[2] * x[6])) * ((x[1] * x[5]) * (x[3] * x[7]));
-        return ((x[0] + x[4]) + (x[2] + x[6])) + ((x[1] + x[5]) + (x[3] + x[7]));
-    };
-    for (int r = tid; r < rows; r += blockDim.x) {
-        float f;
-        if (form == kHGBat) f = hgbat_from_sums(tree(w1, r, false), tree(w2, r, false), D);
-        else if (form == kGriewank) f = fmaf(tree(w1, r, false), 1.f / 4000.f, 1.f - tree(w2, r, true));
-        else f = tree(w1, r, false);
-        S.rowF[r] = (FitT)f;
-    }
+    zrows_to_f<FitT>(S, C, D, Np, rows);
     __syncthreads();
     return true;
 }
