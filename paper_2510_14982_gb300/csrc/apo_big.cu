@@ -50,7 +50,11 @@ namespace apo {
 
 // ----------------------------------------------------------- constants
 constexpr int kBigQPL = kBigMaxDim / 64;   // dimension pairs per lane
-constexpr int kGenWarps = 8;
+// rows per CTA of the row kernels (one warp per row); the generation
+// kernel's 166 registers and 4 staged rows per warp then allow three CTAs
+// (12 warps) per SM
+constexpr int kGenWarps = 4;
+constexpr int kGenThreads = 32 * kGenWarps;
 constexpr int kBM = 128;                    // GEMM tile rows (candidates)
 constexpr int kBK = 64;                     // GEMM K block: 64 fp16 = 128 bytes
 constexpr int kSortChunk = 1024;            // keys per sorted chunk
@@ -176,7 +180,7 @@ __global__ void __launch_bounds__(1024) big_rank_kernel(const BigRun* __restrict
 // up to 16 KB per warp are in flight while the Philox draws and the mask
 // selection run (the populations at ps 10000 do not fit L2, and row gathers
 // from HBM are latency-bound otherwise).
-__global__ void __launch_bounds__(256, 1) big_gen_kernel(const BigRun* __restrict__ runs, int t)
+__global__ void __launch_bounds__(kGenThreads, 3) big_gen_kernel(const BigRun* __restrict__ runs, int t)
 {
     extern __shared__ __align__(16) unsigned char gen_dyn[];
     __shared__ __align__(8) unsigned long long row_bar[kGenWarps];
@@ -251,8 +255,14 @@ __global__ void __launch_bounds__(256, 1) big_gen_kernel(const BigRun* __restric
     const float2* xj = reinterpret_cast<const float2*>(rows_s + 3 * R.Dp);
 
     // per-dimension draws: Rand_d (A) and the mask keys (B) of the whole row
-    uint32_t A[2 * kBigQPL], B[2 * kBigQPL];
+    // The keys stay in registers for the mask selection; Rand_d goes to the
+    // warp's fourth row slot (X_j's, which only the autotrophic mode stages,
+    // and that mode draws no Rand_d), so that the candidate pass below can
+    // be a loop rather than unrolled over the lane's pairs.
+    uint32_t B[2 * kBigQPL];
     uint32_t valid = 0;
+    uint2* As = reinterpret_cast<uint2*>(rows_s + 3 * R.Dp);
+    const bool keep_a = mode != kAutotrophic;
 #pragma unroll
     for (int j = 0; j < kBigQPL; ++j) {
         const int q = lane + 32 * j;
@@ -260,8 +270,9 @@ __global__ void __launch_bounds__(256, 1) big_gen_kernel(const BigRun* __restric
         if (2 * q < D) w = philox((uint32_t)t, (uint32_t)r, (uint32_t)q, kSlotDim, seed, run);
         const bool v0 = 2 * q < D, v1 = 2 * q + 1 < D;
         // slots past D get the key 2^32 - 1, which no threshold counts
-        A[2 * j] = w.x; B[2 * j] = v0 ? w.y : 0xFFFFFFFFu;
-        A[2 * j + 1] = w.z; B[2 * j + 1] = v1 ? w.w : 0xFFFFFFFFu;
+        B[2 * j] = v0 ? w.y : 0xFFFFFFFFu;
+        B[2 * j + 1] = v1 ? w.w : 0xFFFFFFFFu;
+        if (keep_a && v0) As[q] = make_uint2(w.x, w.z);
         valid |= (v0 ? 1u : 0u) << (2 * j);
         valid |= (v1 ? 1u : 0u) << (2 * j + 1);
     }
@@ -293,11 +304,20 @@ __global__ void __launch_bounds__(256, 1) big_gen_kernel(const BigRun* __restric
     const float2* ub2 = reinterpret_cast<const float2*>(R.ub);
     const float2* o2 = reinterpret_cast<const float2*>(R.o);
     const float ysc = R.ysc;
-    // Extra pairs (np > 1, Eq. 6-10) added to acc for the pair (2q, 2q + 1).
-    auto more_pairs = [&](int q, float2& acc, bool autot) {
+    // Eq. 7 / Eq. 10 pair sums of the foraging modes, computed in place of
+    // the staged X_b row before the candidate pass: w_1 (X_a - X_b), then
+    // the pairs k = 2 .. np (np > 1) added in order, each pair's ranks and
+    // weight drawn once per warp.  The candidate pass then reads the sums
+    // and stays short (its body is unrolled over the lane's pairs).
+    if (forage) {
+        float2* acc2 = reinterpret_cast<float2*>(rows_s + 2 * R.Dp);
+        for (int q = lane; 2 * q < D; q += 32) {
+            const float2 va = xa[q], vb = xb[q];
+            acc2[q] = make_float2(w1 * (va.x - vb.x), w1 * (va.y - vb.y));
+        }
         for (int k = 2; k <= np; ++k) {
             uint32_t ea, eb;
-            if (autot) {
+            if (mode == kAutotrophic) {
                 const uint4 pr = philox((uint32_t)t, (uint32_t)r, (uint32_t)(k - 1), kSlotPair, seed, run);
                 ea = perm[idx_draw(pr.x, na)];
                 eb = perm[ob + idx_draw(pr.y, nb)];
@@ -306,41 +326,46 @@ __global__ void __launch_bounds__(256, 1) big_gen_kernel(const BigRun* __restric
                 eb = perm[r + k > ps - 1 ? ps - 1 : r + k];
             }
             const float w2 = expf(-fabsf(R.F[ea] / (R.F[eb] + kEps)));
-            const float2 qa = __ldcg(reinterpret_cast<const float2*>(big_row(R, ea)) + q);
-            const float2 qb = __ldcg(reinterpret_cast<const float2*>(big_row(R, eb)) + q);
-            acc.x = fmaf(w2, qa.x - qb.x, acc.x);
-            acc.y = fmaf(w2, qa.y - qb.y, acc.y);
+            const float2* qa = reinterpret_cast<const float2*>(big_row(R, ea));
+            const float2* qb = reinterpret_cast<const float2*>(big_row(R, eb));
+            for (int q = lane; 2 * q < D; q += 32) {
+                const float2 a = __ldcg(qa + q), b = __ldcg(qb + q);
+                float2 acc = acc2[q];
+                acc.x = fmaf(w2, a.x - b.x, acc.x);
+                acc.y = fmaf(w2, a.y - b.y, acc.y);
+                acc2[q] = acc;
+            }
         }
-    };
+        __syncwarp();
+    }
     // The candidate, one unrolled pass loop per mode (no per-element mode
     // branch); lanes past D skip their pair.
     auto emit = [&](auto mode_c) {
         constexpr int M = decltype(mode_c)::value;
-#pragma unroll
+#pragma unroll 1
         for (int j = 0; j < kBigQPL; ++j) {
             const int q = lane + 32 * j;
-            if (2 * q >= D) continue;
+            if (2 * q >= D) break;
             const float2 lb = __ldg(lb2 + q), ub = __ldg(ub2 + q), o = __ldg(o2 + q);
+            const uint2 a = M == kAutotrophic ? make_uint2(0u, 0u) : As[q];
             float2 x;
             if constexpr (M == kDormancy) {
-                x.x = fmaf(u01(A[2 * j]), ub.x - lb.x, lb.x);                        // Eq. 1
-                x.y = fmaf(u01(A[2 * j + 1]), ub.y - lb.y, lb.y);
+                x.x = fmaf(u01(a.x), ub.x - lb.x, lb.x);                        // Eq. 1
+                x.y = fmaf(u01(a.y), ub.y - lb.y, lb.y);
             } else {
                 const float2 x0 = xi[q];
                 if constexpr (M == kReproduction) {
-                    x.x = x0.x + sg * rho * fmaf(u01(A[2 * j]), ub.x - lb.x, lb.x);  // Eq. 2
-                    x.y = x0.y + sg * rho * fmaf(u01(A[2 * j + 1]), ub.y - lb.y, lb.y);
+                    x.x = x0.x + sg * rho * fmaf(u01(a.x), ub.x - lb.x, lb.x);  // Eq. 2
+                    x.y = x0.y + sg * rho * fmaf(u01(a.y), ub.y - lb.y, lb.y);
                 } else {
-                    const float2 va = xa[q], vb = xb[q];
-                    float2 acc = make_float2(w1 * (va.x - vb.x), w1 * (va.y - vb.y));
-                    if (np > 1) more_pairs(q, acc, M == kAutotrophic);
+                    const float2 acc = xb[q];   // the pair sums
                     if constexpr (M == kAutotrophic) {
                         const float2 vj = xj[q];
                         x.x = x0.x + ff * (vj.x - x0.x + acc.x * inv_np);           // Eq. 6
                         x.y = x0.y + ff * (vj.y - x0.y + acc.y * inv_np);
                     } else {
-                        const float nx = (1.f + sg * u01(A[2 * j]) * nsc) * x0.x;      // Eq. 9
-                        const float ny = (1.f + sg * u01(A[2 * j + 1]) * nsc) * x0.y;
+                        const float nx = (1.f + sg * u01(a.x) * nsc) * x0.x;      // Eq. 9
+                        const float ny = (1.f + sg * u01(a.y) * nsc) * x0.y;
                         x.x = x0.x + ff * (nx - x0.x + acc.x * inv_np);              // Eq. 8
                         x.y = x0.y + ff * (ny - x0.y + acc.y * inv_np);
                     }
@@ -1039,7 +1064,7 @@ apo_status big_run_group(const std::vector<BigSpec>& specs, cudaStream_t st, cha
     };
     if (rc == APO_OK && e == cudaSuccess) {
         if (eval_only) {
-            big_pack_kernel<<<g_rows, 256, 0, st>>>(d_runs);
+            big_pack_kernel<<<g_rows, kGenThreads, 0, st>>>(d_runs);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = gemm();
             if (e == cudaSuccess) {
@@ -1051,7 +1076,7 @@ apo_status big_run_group(const std::vector<BigSpec>& specs, cudaStream_t st, cha
                                !(flags & (kBigStepOut | kBigStateOut)) && (flags & kBigInit);
             if (timed) cudaEventRecord(big_timing_before(), st);
             if (flags & kBigInit) {
-                big_init_kernel<<<g_rows, 256, 0, st>>>(d_runs);
+                big_init_kernel<<<g_rows, kGenThreads, 0, st>>>(d_runs);
                 e = cudaGetLastError();
                 if (e == cudaSuccess) e = gemm();
                 if (e == cudaSuccess) {
@@ -1076,7 +1101,7 @@ apo_status big_run_group(const std::vector<BigSpec>& specs, cudaStream_t st, cha
                 e = rank(t);
                 if (e == cudaSuccess)
                     e = timer.run(kStageGen, [&] {
-                        big_gen_kernel<<<g_rows, 256, gen_smem, st>>>(d_runs, t);
+                        big_gen_kernel<<<g_rows, kGenThreads, gen_smem, st>>>(d_runs, t);
                         return cudaGetLastError();
                     });
                 if (e == cudaSuccess) e = gemm();
