@@ -67,9 +67,6 @@ struct BigSpec {
     float* F_out;
 };
 
-// GEMM N tile (64 or 128) for a population and dimension.
-int big_tile_n(int ps, int D);
-
 // Runs a group of at most kBigMaxRuns runs sharing (t_begin, t_end, flags)
 // on `st` (stream-ordered; the workspace is allocated and freed in stream
 // order).  err receives a message when the result is not APO_OK.
