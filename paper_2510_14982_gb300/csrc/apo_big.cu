@@ -11,19 +11,23 @@
 //                         own chunk plus the number of smaller keys in every
 //                         other chunk (binary searches in shared memory);
 //                         the new rank -> slot permutation, the curve;
-//   3. big_gen_kernel     one warp per candidate (Eq. 1-10, 12-13, clamp): a
-//                         row's 1024 per-dimension draws and mask keys in
-//                         registers, the mask by k-selection over the warp,
-//                         then the candidate pair by pair; the fp32 row goes
-//                         to the slot's other population buffer, y = ysc (x -
-//                         o) as fp16 hi + lo parts to the GEMM operand;
-//   4. big_gemm_kernel    Z = Y B^T on the tensor cores: 128 x BN tiles, the
-//                         operands staged by TMA (cp.async.bulk.tensor, 128-byte
-//                         swizzle) in a multi-stage mbarrier pipeline, three
-//                         tcgen05.mma per K step (y_lo B_hi, y_hi B_lo, y_hi
-//                         B_hi) into a TMEM accumulator, and the objective's
-//                         per-row partial sums computed from TMEM in the
-//                         epilogue (z never goes to memory);
+//   3. big_gen_kernel     one warp per candidate (Eq. 1-10, 12-13, clamp):
+//                         the gathered rows staged in shared memory by bulk
+//                         copies, a row's mask keys in registers and its
+//                         Rand_d words in shared memory, the mask by
+//                         k-selection over the warp, the foraging pair sums in
+//                         one pass, then the candidate pair by pair; the fp32
+//                         row goes to the slot's other population buffer,
+//                         y = ysc (x - o) as fp16 hi + lo parts to the GEMM
+//                         operand;
+//   4. big_gemm_kernel    Z = Y B^T on the tensor cores, persistent (one CTA
+//                         per SM over 128 x 128 tiles): the operands staged
+//                         by TMA (cp.async.bulk.tensor, 128-byte swizzle) in a
+//                         multi-stage mbarrier pipeline, three tcgen05.mma per
+//                         K step (y_lo B_hi, y_hi B_lo, y_hi B_hi) into TMEM
+//                         accumulators, and the objective's per-row partial
+//                         sums computed from TMEM in the epilogue, overlapping
+//                         the next tile's MMAs (z never goes to memory);
 //   5. big_finalize_kernel  the partial sums combined per row in tile order,
 //                         the greedy replacement of Algorithm 1 (a slot's
 //                         buffer bit flips when its candidate wins).
@@ -37,8 +41,8 @@
 
 #include <algorithm>
 #include <cstdio>
-#include <type_traits>
 #include <cstring>
+#include <type_traits>
 #include <mutex>
 #include <vector>
 
@@ -391,13 +395,13 @@ __global__ void __launch_bounds__(kGenThreads, 3) big_gen_kernel(const BigRun* _
     }
 }
 
-// 4. The rotation GEMM with the objective epilogue.  Tile (blockIdx.x,
-// blockIdx.y) of run blockIdx.z: candidate rows m0 .. m0 + 127, output
-// dimensions n0 .. n0 + BN - 1.  Warp 0 lane 0 issues the TMA loads, warp 1
-// lane 0 the MMAs, warp 2 allocates the accumulator; all four warps read it
-// back (thread = candidate row) and reduce the objective's terms of their
-// columns into per-row partial sums.  Every wait has a time limit; on
-// timeout the run's status is set and the CTA leaves after its copies landed.
+// 4. The rotation GEMM with the objective epilogue.  A tile is candidate
+// rows m0 .. m0 + 127 and output dimensions n0 .. n0 + BN - 1 of one run; the
+// persistent CTAs walk the tiles (roles and hand-overs below the kernel's
+// constants).  The epilogue reads the accumulators back (thread = candidate
+// row) and reduces the objective's terms of its columns into per-row partial
+// sums.  Every wait has a time limit; on timeout the run's status is set and
+// the CTA leaves after its copies landed and its TMEM is freed.
 struct BigMaps {
     CUtensorMap yh[kBigMaxRuns], yl[kBigMaxRuns], gh[kBigMaxRuns], gl[kBigMaxRuns];
 };
