@@ -245,6 +245,13 @@ __device__ __forceinline__ float rast_term(float v)
     return fmaf(v, v, fmaf(-10.f, cos2pi(v), 10.f));
 }
 
+// floor(i / d) for 0 <= i < 2^16 and 1 <= d < 2^16 by one multiply-high with
+// m = div_magic(d) = floor((2^32 - 1) / d) + 1 (m >= 2^32 / d and the error
+// i (m - 2^32 / d) / 2^32 < i / 2^32 < 1 / d cannot reach the next integer),
+// for the flat index loops whose row length is only known at run time.
+__device__ __forceinline__ uint32_t div_magic(uint32_t d) { return d == 1u ? 0u : 0xFFFFFFFFu / d + 1u; }
+__device__ __forceinline__ uint32_t div_small(uint32_t i, uint32_t m) { return m == 0u ? i : __umulhi(i, m); }
+
 // ------------------------------------------------------- fitness ordering
 __device__ __forceinline__ uint32_t ord_key(float f)
 {

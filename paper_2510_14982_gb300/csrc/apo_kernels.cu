@@ -241,8 +241,9 @@ __device__ __forceinline__ void run_one(const ApoRun& R, int local, unsigned cha
                 Fs[cur ^ 1][perm[c0 + row]] = fn < fo ? fn : fo;
             }
             const int g4 = Dp >> 2;
+            const uint32_t g4m = div_magic((uint32_t)g4);
             for (int i = tid; i < rows * g4; i += blockDim.x) {
-                const int row = i / g4, v = i - row * g4;
+                const int row = (int)div_small((uint32_t)i, g4m), v = i - row * g4;
                 const bool acc = S.rowF[row] < S.rowF[CH + row];
                 const float4* src = reinterpret_cast<const float4*>((acc ? S.Xc : S.Xo) + (size_t)row * Dp);
                 float4* dst = reinterpret_cast<float4*>(Xs[cur ^ 1] + (size_t)perm[c0 + row] * Dp);

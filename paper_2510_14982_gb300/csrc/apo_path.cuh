@@ -435,8 +435,9 @@ __device__ __forceinline__ void eval_chunk(const ApoRun& R, const Smem<FitT>& S,
             tile_gemm_f16x3<false>(S.Xc, Dp, o, C.Bh, C.Bl, P.bws, C.ysc, C.zsc, S.Zc, Np, rows, D);
         } else {
             // no rotation: YT[d][row] = x - o (zero beyond D)
+            const uint32_t chm = div_magic((uint32_t)CH);
             for (int i = threadIdx.x; i < CH * Dp; i += blockDim.x) {
-                const int d = i / CH, row = i - d * CH;
+                const int d = (int)div_small((uint32_t)i, chm), row = i - d * CH;
                 S.Yc[i] = (d < D && row < rows) ? S.Xc[(size_t)row * Dp + d] - o[d] : 0.f;
             }
         }

@@ -125,9 +125,11 @@ __device__ bool eval_chunk_tc(const ApoRun& R, const Smem<FitT>& S, int rows, Tc
     const float ysc = C.ysc;
     unsigned char* yh = S.TY;
     unsigned char* yl = S.TY + (size_t)kTcN * Np * 2;
+    const uint32_t gm = div_magic((uint32_t)(8 * nkb));
     for (int i = tid; i < kTcN * nkb; i += blockDim.x) {
-        const int r = (i & 7) + 8 * (i / (8 * nkb));
-        const int kb = (i >> 3) % nkb;
+        const int grp = (int)div_small((uint32_t)i, gm);   // 8-row group
+        const int r = (i & 7) + 8 * grp;
+        const int kb = (i >> 3) - grp * nkb;
         const float4* xr = reinterpret_cast<const float4*>(S.Xc + (size_t)r * Dp + 8 * kb);
         const float4* orow = reinterpret_cast<const float4*>(S.o + 8 * kb);
         const float4 x0 = xr[0], x1 = xr[1], o0 = orow[0], o1 = orow[1];
