@@ -251,6 +251,13 @@ __device__ __forceinline__ float rast_term(float v)
 // for the flat index loops whose row length is only known at run time.
 __device__ __forceinline__ uint32_t div_magic(uint32_t d) { return d == 1u ? 0u : 0xFFFFFFFFu / d + 1u; }
 __device__ __forceinline__ uint32_t div_small(uint32_t i, uint32_t m) { return m == 0u ? i : __umulhi(i, m); }
+// The same for any 32-bit i with a 64-bit m = floor((2^64 - 1) / d) + 1
+// (error below i / 2^64 < 1 / d): one 64-bit multiply-high.
+__device__ __forceinline__ unsigned long long magic64(uint32_t d) { return d <= 1u ? 0ull : ~0ull / d + 1ull; }
+__device__ __forceinline__ uint32_t div_magic64(uint32_t i, unsigned long long m)
+{
+    return m == 0ull ? i : (uint32_t)__umul64hi((unsigned long long)i, m);
+}
 
 // ------------------------------------------------------- fitness ordering
 __device__ __forceinline__ uint32_t ord_key(float f)

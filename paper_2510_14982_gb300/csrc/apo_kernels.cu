@@ -207,6 +207,7 @@ __device__ __forceinline__ void run_one(const ApoRun& R, int local, unsigned cha
 
     int cur = 0, pc = 0;
     KT* keys = static_cast<KT*>(S.keys);
+    const unsigned long long psm = magic64((uint32_t)ps);
     for (int t = R.t_begin; t <= R.t_end; ++t) {
         // Algorithm 1: sort by fitness; ties keep the previous order.
         const uint32_t* perm = S.perm[pc];
@@ -224,7 +225,7 @@ __device__ __forceinline__ void run_one(const ApoRun& R, int local, unsigned cha
         const bool curve_w = local == 0 && tid == 0 && R.curve != nullptr;
         const FitT curve_v = curve_w ? ldst(Fs[cur] + perm[0], res) : (FitT)0;
 
-        const IterScal is = iter_scal(R, t);
+        const IterScal is = iter_scal(R, t, psm);
         for (int c0 = r0; c0 < r1; c0 += CH) {
             const int rows = min(CH, r1 - c0);
             for (int row = warp; row < rows; row += nw)
@@ -649,11 +650,11 @@ __device__ __forceinline__ void run_grid(const ApoRun& R, int local, unsigned ch
         }
 
         // the own positions: generate, evaluate, replace
-        const IterScal is = iter_scal(R, t);
+        const IterScal is = iter_scal(R, t, 0ull);
         for (int c0 = 0; c0 < nown; c0 += CH) {
             const int rows = min(CH, nown - c0);
             for (int row = warp; row < rows; row += nw)
-                gen_step_row<FitT, QPL>(R, S, Xs[0], Xs[1], Fs[cur], perm, false, false, t, is, pos_of(c0 + row),
+                gen_step_row<FitT, QPL, false>(R, S, Xs[0], Xs[1], Fs[cur], perm, false, false, t, is, pos_of(c0 + row),
                                         drs[c0 + row], row);
             __syncthreads();
             if (!evaluate(rows)) return;

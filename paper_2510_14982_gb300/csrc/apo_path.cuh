@@ -525,13 +525,16 @@ __device__ __forceinline__ void gen_init_row(const ApoRun& R, const Smem<FitT>& 
 // The iteration's scalars of Eq. 7, Eq. 9 and Eq. 11-13 (p_ah threshold, the
 // foraging factor's scale and the neighbourhood scale), loaded once per
 // iteration by the caller rather than once per candidate row.
+// psm: the run's reciprocal of ps for the mask sizes of Eq. 5 (magic64),
+// computed once per launch (0 where the caller divides).
 struct IterScal {
     uint32_t thr_ah;
     float fsc, nsc;
+    unsigned long long psm;
 };
-__device__ __forceinline__ IterScal iter_scal(const ApoRun& R, int t)
+__device__ __forceinline__ IterScal iter_scal(const ApoRun& R, int t, unsigned long long psm)
 {
-    return IterScal{R.thr_ah[t], R.fsc[t], R.nsc[t]};
+    return IterScal{R.thr_ah[t], R.fsc[t], R.nsc[t], psm};
 }
 
 // One candidate (rank r, 0-based) by one warp: mode selection (Eq. 12-13,
@@ -545,7 +548,7 @@ __device__ __forceinline__ IterScal iter_scal(const ApoRun& R, int t)
 // computed once per warp, one Philox call per lane; the gathered rows are
 // requested before the per-dimension draws and the mask selection so that
 // their latency overlaps that arithmetic.
-template <typename FitT, int QPL>
+template <typename FitT, int QPL, bool kMagicK = true>
 __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* __restrict__ X,
                              const float* __restrict__ X1, const FitT* __restrict__ F, const uint32_t* perm,
                              bool res, bool keep_old, int t, const IterScal& is, int r, uint32_t drs, int row,
@@ -655,7 +658,10 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
         const int k = (int)(((unsigned long long)D * m24p1(sc2.x) + 0xFFFFFFull) >> 24);
         mask = warp_kselect_interp<QPL>(B, valid, k, D);
     } else if (forage) {
-        const int k = (D * (r + 1) + ps - 1) / ps;
+        // ceil(D (r + 1) / ps): by the run's reciprocal, or (kMagicK false:
+        // the grid kernel, measured 0.6% faster so) by a division
+        const int k = kMagicK ? (int)div_magic64((uint32_t)(D * (r + 1) + ps - 1), is.psm)
+                              : (D * (r + 1) + ps - 1) / ps;
         mask = warp_kselect_interp<QPL>(B, valid, k, D);
     }
 

@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(kSurThreads) surr_gen_kernel(const ApoRun* __r
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int D = R.prob.D, Dp = R.prob.Dp, CH = R.plan.chunk;
     const int nrow = R.ps * k;
-    const IterScal is = iter_scal(R, t);
+    const IterScal is = iter_scal(R, t, magic64((uint32_t)R.ps));
     for (int c0 = blockIdx.x * CH; c0 < nrow; c0 += gridDim.x * CH) {
         const int rows = min(CH, nrow - c0);
         for (int row = warp; row < rows; row += nw) {
