@@ -523,18 +523,18 @@ __device__ __forceinline__ void gen_init_row(const ApoRun& R, const Smem<FitT>& 
 }
 
 // The iteration's scalars of Eq. 7, Eq. 9 and Eq. 11-13 (p_ah threshold, the
-// foraging factor's scale and the neighbourhood scale), loaded once per
-// iteration by the caller rather than once per candidate row.
+// foraging factor's scale, the neighbourhood scale and 1 / np), loaded once
+// per iteration by the caller rather than once per candidate row.
 // psm: the run's reciprocal of ps for the mask sizes of Eq. 5 (magic64),
 // computed once per launch (0 where the caller divides).
 struct IterScal {
     uint32_t thr_ah;
-    float fsc, nsc;
+    float fsc, nsc, inv_np;
     unsigned long long psm;
 };
 __device__ __forceinline__ IterScal iter_scal(const ApoRun& R, int t, unsigned long long psm)
 {
-    return IterScal{R.thr_ah[t], R.fsc[t], R.nsc[t], psm};
+    return IterScal{R.thr_ah[t], R.fsc[t], R.nsc[t], 1.f / (float)R.np, psm};
 }
 
 // One candidate (rank r, 0-based) by one warp: mode selection (Eq. 12-13,
@@ -562,7 +562,7 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     const uint32_t seed = R.seed, run = R.run;
     const uint32_t thr_ah = is.thr_ah;
     const float fsc = is.fsc, nsc = is.nsc;
-    const float inv_np = 1.f / (float)np;
+    const float inv_np = is.inv_np;
     // Per-protozoon draws, from lanes jb + u: u = 0 SCAL, u = 1 SCAL2,
     // u = 2 + k PAIR k.  The last per-dimension call of a lane covers pairs
     // q = lane + 32 (QPL - 1), of which only q < ceil(D / 2) exist; when at
