@@ -220,8 +220,17 @@ def run_batched(args):
     dev = torch.device("cuda", local)
     bx = torch.zeros((n, 50), device=dev)
     bf = torch.zeros(n, dtype=torch.float64, device=dev)
-    b = apo.apo_batch_create(probs, prms, bx, 50, bf)
-    chosen = b.autotune(probe_iters=40)
+    if args.batch_config:
+        # a fixed mapping instead of the autotuner's choice (reproducible
+        # profiling: under a profiler the autotuner's timings are distorted)
+        smem, cps_sm, cl_ps, cl_sz = (int(v) for v in args.batch_config.split(","))
+        b = apo.apo_batch_create(probs, prms, bx, 50, bf, smem_budget=smem, ctas_per_sm=cps_sm, cluster_ps=cl_ps,
+                                 cluster_size=cl_sz)
+        chosen = {"smem_budget": smem, "ctas_per_sm": cps_sm, "cluster_ps": cl_ps, "cluster_size": cl_sz,
+                  "fixed": True}
+    else:
+        b = apo.apo_batch_create(probs, prms, bx, 50, bf)
+        chosen = b.autotune(probe_iters=40)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         b.launch(stream)
@@ -794,6 +803,8 @@ def main():
     ap.add_argument("--seeds", type=int, default=5, help="surrogate: seeds for the time-to-target comparison")
     ap.add_argument("--runs", type=int, default=1024, help="batched workload: number of runs")
     ap.add_argument("--per-run-sample", type=int, default=24, help="batched: runs timed with one launch each")
+    ap.add_argument("--batch-config", default="",
+                    help="batched: fixed SMEM_BUDGET,CTAS_PER_SM,CLUSTER_PS,CLUSTER_SIZE instead of autotuning")
     ap.add_argument("--iters", type=int, default=0, help="override the iteration count (profiling)")
     ap.add_argument("--ps", type=int, default=0, help="table2: one population instead of 1000 and 10000")
     ap.add_argument("--ref-iters", type=int, default=2, help="oracle iterations of each run per --impl reference step")
