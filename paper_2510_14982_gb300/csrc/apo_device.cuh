@@ -214,7 +214,7 @@ __device__ __forceinline__ float sign_draw(uint32_t r) { return (r & 1u) ? -1.f 
 // (-1)^n (2 pi)^(2n) / (2n)!, truncation below (pi/2)^14 / 14! < 7e-9), so
 // the result is within about 2e-7 of the exact value, at a third of the
 // instructions of a general cosine.
-__device__ __forceinline__ float cos2pi(float v)
+__host__ __device__ __forceinline__ float cos2pi(float v)
 {
     const float r = fabsf(v - rintf(v));
     const bool flip = r > 0.25f;
@@ -234,13 +234,13 @@ __device__ __forceinline__ float cos2pi(float v)
 // z_{d+1})) and of the Rastrigin form, with every multiply-add written out,
 // so that each kernel that evaluates them (whatever the compiler would fuse
 // in its context) rounds them the same way.
-__device__ __forceinline__ float rosen_term(float v, float vn)
+__host__ __device__ __forceinline__ float rosen_term(float v, float vn)
 {
     const float a = fmaf(-v, v, vn);
     const float b = v - 1.f;
     return fmaf(100.f * a, a, b * b);
 }
-__device__ __forceinline__ float rast_term(float v)
+__host__ __device__ __forceinline__ float rast_term(float v)
 {
     return fmaf(v, v, fmaf(-10.f, cos2pi(v), 10.f));
 }
@@ -248,15 +248,27 @@ __device__ __forceinline__ float rast_term(float v)
 // floor(i / d) for 0 <= i < 2^16 and 1 <= d < 2^16 by one multiply-high with
 // m = div_magic(d) = floor((2^32 - 1) / d) + 1 (m >= 2^32 / d and the error
 // i (m - 2^32 / d) / 2^32 < i / 2^32 < 1 / d cannot reach the next integer),
-// for the flat index loops whose row length is only known at run time.
-__device__ __forceinline__ uint32_t div_magic(uint32_t d) { return d == 1u ? 0u : 0xFFFFFFFFu / d + 1u; }
-__device__ __forceinline__ uint32_t div_small(uint32_t i, uint32_t m) { return m == 0u ? i : __umulhi(i, m); }
+// for the flat index loops whose row length is only known at run time.  (Host
+// versions of the multiply-highs serve the host-side checks.)
+__host__ __device__ __forceinline__ uint32_t div_magic(uint32_t d) { return d == 1u ? 0u : 0xFFFFFFFFu / d + 1u; }
+__host__ __device__ __forceinline__ uint32_t div_small(uint32_t i, uint32_t m)
+{
+#ifdef __CUDA_ARCH__
+    return m == 0u ? i : __umulhi(i, m);
+#else
+    return m == 0u ? i : (uint32_t)(((unsigned long long)i * m) >> 32);
+#endif
+}
 // The same for any 32-bit i with a 64-bit m = floor((2^64 - 1) / d) + 1
 // (error below i / 2^64 < 1 / d): one 64-bit multiply-high.
-__device__ __forceinline__ unsigned long long magic64(uint32_t d) { return d <= 1u ? 0ull : ~0ull / d + 1ull; }
-__device__ __forceinline__ uint32_t div_magic64(uint32_t i, unsigned long long m)
+__host__ __device__ __forceinline__ unsigned long long magic64(uint32_t d) { return d <= 1u ? 0ull : ~0ull / d + 1ull; }
+__host__ __device__ __forceinline__ uint32_t div_magic64(uint32_t i, unsigned long long m)
 {
+#ifdef __CUDA_ARCH__
     return m == 0ull ? i : (uint32_t)__umul64hi((unsigned long long)i, m);
+#else
+    return m == 0ull ? i : (uint32_t)(((unsigned __int128)i * m) >> 64);
+#endif
 }
 
 // ------------------------------------------------------- fitness ordering
