@@ -420,10 +420,12 @@ static __constant__ RecipTable kRecip = make_recip_table();
 // boundary would give another count and take the exact bitwise descent, as
 // does no convergence within ten counts).  n = number of valid slots (<= 1024);
 // slots outside `valid` must hold the key 2^32 - 1, which no threshold counts.
-template <int QPL>
+// kAdjust = 2: a correction step costs about as much as a count, and counts
+// close in faster from farther away (measured: 55.4 ms per scale step at 2,
+// 55.9 at 4, 57.8 at 8, 59.0 at 16).
+template <int QPL, int kAdjust = 2>
 __device__ uint32_t warp_kselect_interp(const uint32_t (&key)[2 * QPL], uint32_t valid, int k, int n)
 {
-    constexpr int kAdjust = 8;
     if (k <= 0) return 0;
     if (k >= n) return valid;
     // invariant: clo = #(keys < lo) < k < chi = #(keys <= hm); thresholds are
