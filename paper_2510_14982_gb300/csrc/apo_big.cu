@@ -281,13 +281,15 @@ __global__ void __launch_bounds__(kGenThreads, 3) big_gen_kernel(const BigRun* _
         valid |= (v0 ? 1u : 0u) << (2 * j);
         valid |= (v1 ? 1u : 0u) << (2 * j + 1);
     }
+    // corrections only within one key of k (at 32 keys per lane a correction
+    // step costs more than a count: 290 against 297 us per iteration with 2)
     uint32_t mask = 0;
     if (mode == kReproduction) {
         const int k = (int)(((unsigned long long)D * m24p1(s2x) + 0xFFFFFFull) >> 24);
-        mask = warp_kselect_interp<kBigQPL>(B, valid, k, D);
+        mask = warp_kselect_interp<kBigQPL, 1>(B, valid, k, D);
     } else if (forage) {
         const int k = (D * (r + 1) + ps - 1) / ps;
-        mask = warp_kselect_interp<kBigQPL>(B, valid, k, D);
+        mask = warp_kselect_interp<kBigQPL, 1>(B, valid, k, D);
     }
     const float ff = forage ? u01(sc.y) * fsc : 0.f;
     const float sg = sign_draw(sc.z);
