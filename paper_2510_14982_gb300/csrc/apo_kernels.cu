@@ -229,7 +229,7 @@ __device__ __forceinline__ void run_one(const ApoRun& R, int local, unsigned cha
         for (int c0 = r0; c0 < r1; c0 += CH) {
             const int rows = min(CH, r1 - c0);
             for (int row = warp; row < rows; row += nw)
-                gen_step_row<FitT, QPL>(R, S, Xs[cur], nullptr, Fs[cur], perm, res, true, t, is, c0 + row,
+                gen_step_row<FitT, QPL, true, 4>(R, S, Xs[cur], nullptr, Fs[cur], perm, res, true, t, is, c0 + row,
                                         dr_state(R, t, c0 + row), row);
             __syncthreads();
             eval_chunk<FitT>(R, S, rows);

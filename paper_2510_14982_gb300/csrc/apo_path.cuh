@@ -548,7 +548,7 @@ __device__ __forceinline__ IterScal iter_scal(const ApoRun& R, int t, unsigned l
 // computed once per warp, one Philox call per lane; the gathered rows are
 // requested before the per-dimension draws and the mask selection so that
 // their latency overlaps that arithmetic.
-template <typename FitT, int QPL, bool kMagicK = true>
+template <typename FitT, int QPL, bool kMagicK = true, int kAdjust = 2>
 __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& S, const float* __restrict__ X,
                              const float* __restrict__ X1, const FitT* __restrict__ F, const uint32_t* perm,
                              bool res, bool keep_old, int t, const IterScal& is, int r, uint32_t drs, int row,
@@ -656,13 +656,13 @@ __device__ __forceinline__ void gen_step_row(const ApoRun& R, const Smem<FitT>& 
     uint32_t mask = 0;
     if (mode == kReproduction) {
         const int k = (int)(((unsigned long long)D * m24p1(sc2.x) + 0xFFFFFFull) >> 24);
-        mask = warp_kselect_interp<QPL>(B, valid, k, D);
+        mask = warp_kselect_interp<QPL, kAdjust>(B, valid, k, D);
     } else if (forage) {
         // ceil(D (r + 1) / ps): by the run's reciprocal, or (kMagicK false:
         // the grid kernel, measured 0.6% faster so) by a division
         const int k = kMagicK ? (int)div_magic64((uint32_t)(D * (r + 1) + ps - 1), is.psm)
                               : (D * (r + 1) + ps - 1) / ps;
-        mask = warp_kselect_interp<QPL>(B, valid, k, D);
+        mask = warp_kselect_interp<QPL, kAdjust>(B, valid, k, D);
     }
 
     // Eq. 7 / Eq. 10 weights and the pair sums
